@@ -1,0 +1,354 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a textbook
+or library routine, a closed form, an invariant the paper proves, a number
+the paper prints, or brute force on a tiny grid.  No GPU is involved.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+from scipy.special import digamma
+
+import oracle
+from tests import inputs
+from tests.gaussians import Gauss1D, coherent_state, product_on_grid
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.asarray(b).ravel())
+
+
+# --------------------------------------------------------------------------
+# Discrete Fourier transform (Sec. II.B)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 64, 256, 1024, 6, 12, 18, 24, 48, 96])
+def test_dft_matches_numpy_and_direct_sum(n):
+    x = inputs.random_state(n, seed=n)
+    fwd = oracle.dft1d(x, -1)
+    assert np.allclose(fwd, np.fft.fft(x) / np.sqrt(n), atol=1e-14, rtol=0)
+    assert np.allclose(fwd, oracle.dft1d_direct(x, -1), atol=1e-13, rtol=0)
+    inv = oracle.dft1d(fwd, +1)
+    assert np.allclose(inv, x, atol=1e-14, rtol=0)
+    assert abs(np.sum(abs(fwd) ** 2) - np.sum(abs(x) ** 2)) < 1e-14  # Parseval
+
+
+# --------------------------------------------------------------------------
+# Shifted transform f(q,p) (eq:F_defintion, eq:t_definition)
+# --------------------------------------------------------------------------
+
+def kernel_matrix(g, q, p):
+    """N^{-1/2} e^{-i p^K . q^J / hbar}: eq:fourier_pos_to_mom with the
+    C_q, C_p scalings folded in (C_q C_p = 1/N)."""
+    qa = np.meshgrid(*g.qaxes(q), indexing="ij")
+    pa = np.meshgrid(*[p[l] + (np.arange(g.N[l]) - g.N[l] / 2) * g.dp[l] for l in range(g.D)],
+                     indexing="ij")
+    X = np.stack([a.ravel() for a in qa], 1)
+    P = np.stack([a.ravel() for a in pa], 1)
+    return np.exp(-1j * (P @ X.T) / g.hbar) / np.sqrt(g.npts)
+
+
+@pytest.mark.parametrize("N,hbar", [((16,), 1.0), ((8, 6), 0.7), ((4, 4, 4), 1.0), ((12,), 2.0)])
+def test_shifted_transform_literal_fused_and_kernel(N, hbar):
+    D = len(N)
+    g = oracle.Grid(N, dq=np.linspace(0.3, 0.5, D), hbar=hbar)
+    q, p = inputs.random_centre(D, seed=7)
+    x = inputs.random_state(N, seed=3)
+    fused = g.apply_f(q, p, x, -1)
+    dense = g.apply_f(q, p, x, -1, dense=True)
+    assert rel(fused, dense) < 1e-13
+    F = kernel_matrix(g, q, p)
+    assert rel(dense.ravel(), F @ x.ravel()) < 1e-12
+    # f~ = f^dagger = f^{-1} (eq:F_inv_definition)
+    back = g.apply_f(q, p, fused, +1)
+    assert rel(back, x) < 1e-13
+    assert rel(g.apply_f(q, p, x, +1, dense=True).ravel(), F.conj().T @ x.ravel()) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Substeps on a fixed grid vs brute-force matrix exponentials
+# --------------------------------------------------------------------------
+
+def hh_grid_2d():
+    g = oracle.Grid((8, 8), dq=(0.8, 0.7), minv=(1.0, 0.8))
+    g.set_potential(oracle.POT_HENON_HEILES, [0.2])
+    return g
+
+
+def hamiltonian_matrix(g, q, p):
+    F = kernel_matrix(g, q, p)
+    pa = np.meshgrid(*[p[l] + (np.arange(g.N[l]) - g.N[l] / 2) * g.dp[l] for l in range(g.D)],
+                     indexing="ij")
+    P = np.stack([a.ravel() for a in pa], 1)
+    T = 0.5 * np.einsum("ka,ab,kb->k", P, g.minv, P)
+    X = np.stack([a.ravel() for a in np.meshgrid(*g.qaxes(q), indexing="ij")], 1)
+    V, _ = g.potential(X)
+    return F.conj().T @ np.diag(T) @ F, np.diag(V)
+
+
+def test_fixed_grid_kinetic_substep_is_matrix_exponential():
+    g = hh_grid_2d()
+    q, p = np.array([0.3, -0.2]), np.array([0.5, 0.1])
+    u0 = inputs.random_state(g.N, seed=11)
+    g.set_u(u0)
+    g.set_state(g.get_state()[0], q, p)
+    g.set_u(u0)
+    Tm, Vm = hamiltonian_matrix(g, q, p)
+    g.substep_T(0.37, oracle.GRID_FIXED)
+    assert rel(g.get_u().ravel(), expm(-1j * 0.37 * Tm) @ u0.ravel()) < 1e-12
+    g.substep_V(0.21, oracle.GRID_FIXED)
+    ref = expm(-1j * 0.21 * Vm) @ expm(-1j * 0.37 * Tm) @ u0.ravel()
+    assert rel(g.get_u().ravel(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("scheme,order", [("strang", 2), ("yoshida4", 4), ("suzuki4", 4),
+                                          ("yoshida6", 6)])
+def test_fixed_grid_composition_order_vs_expm(scheme, order):
+    g = hh_grid_2d()
+    q, p = np.array([0.3, -0.2]), np.array([0.5, 0.1])
+    u0 = inputs.random_state(g.N, seed=5)
+    Tm, Vm = hamiltonian_matrix(g, q, p)
+    t = 1.0
+    exact = expm(-1j * t * (Tm + Vm)) @ u0.ravel()
+    errs = []
+    dts = [0.25, 0.125, 0.0625] if order < 6 else [0.125, 0.0625, 0.03125]
+    for dt in dts:
+        g.set_u(u0)
+        g.set_state(g.get_state()[0], q, p)
+        g.set_u(u0)
+        g.propagate(round(t / dt), dt, scheme, oracle.SPLIT_TVT, oracle.GRID_FIXED)
+        errs.append(rel(g.get_u().ravel(), exact))
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(dts))
+    assert np.all(np.abs(slopes - order) < 0.35), (errs, slopes)
+
+
+# --------------------------------------------------------------------------
+# Moving grid vs closed-form Gaussian flows
+# --------------------------------------------------------------------------
+
+def run_split_gaussians(gs, ms, ks, cs, dt, steps, gammas):
+    """Compose the exact 1D Gaussian flows in TVT order (eq:comp_TVT)."""
+    for _ in range(steps):
+        for gm in gammas:
+            h = gm * dt
+            for G, m in zip(gs, ms):
+                G.kinetic(h / 2, m)
+            for G, k, c in zip(gs, ks, cs):
+                G.potential(h, k, c)
+            for G, m in zip(gs, ms):
+                G.kinetic(h / 2, m)
+
+
+@pytest.mark.parametrize("scheme", ["strang", "yoshida4"])
+def test_moving_grid_matches_discrete_gaussian_closed_form(scheme):
+    # 1D, omega = 1, spacing 0.3, 64 points: the packet is < 1e-20 at the edges.
+    N, dq, dt, steps = (64,), (0.3,), 0.01, 1000 if scheme == "strang" else 300
+    q0, p0 = 1.0, 0.5
+    g = oracle.Grid(N, dq)
+    g.set_potential(oracle.POT_HARMONIC, [1.0, 0.0])
+    g.set_separable([("gauss", q0, p0, 1.0)], [q0], [p0])
+    g.propagate(steps, dt, scheme)
+    psi, q, p, t = g.get_state()
+    G = Gauss1D(q0, p0, 1.0)
+    run_split_gaussians([G], [1.0], [1.0], [0.0], dt, steps, oracle.scheme(scheme))
+    exact = G(g.qaxes(q)[0])
+    assert rel(psi, exact) < 1e-12
+    # the grid centre equals the Gaussian's centre (position Verlet, Sec. II.H)
+    assert abs(q[0] - G.xc) < 1e-12 and abs(p[0] - G.pi) < 1e-12
+    assert abs(t - steps * dt) < 1e-9
+
+
+def test_moving_grid_2d_mass_hbar_and_centre_closed_form():
+    hbar = 0.7
+    minv = np.array([0.5, 2.0])
+    k = np.array([1.3, 0.6])
+    c = np.array([0.2, -0.1])
+    q0, p0 = np.array([1.1, -0.4]), np.array([0.3, 0.6])
+    omega = np.sqrt(k * minv)
+    sig = np.sqrt(hbar / (omega / minv))  # sigma^2 = hbar/(m omega)
+    N, dq = (48, 96), (0.25, 0.22)
+    g = oracle.Grid(N, dq, minv=minv, hbar=hbar)
+    g.set_potential(oracle.POT_HARMONIC, list(np.diag(k).ravel()) + list(c))
+    g.set_separable([("gauss", q0[l], p0[l], sig[l]) for l in range(2)], q0, p0)
+    dt, steps = 0.02, 200
+    g.propagate(steps, dt, "yoshida4")
+    psi, q, p, _ = g.get_state()
+    gs = [Gauss1D(q0[l], p0[l], sig[l], hbar) for l in range(2)]
+    run_split_gaussians(gs, 1 / minv, k, c, dt, steps, oracle.scheme("yoshida4"))
+    exact = product_on_grid(gs, g.qaxes(q))
+    assert rel(psi, exact) < 1e-11
+    assert np.allclose(q, [G.xc for G in gs], atol=1e-11, rtol=0)
+    assert np.allclose(p, [G.pi for G in gs], atol=1e-11, rtol=0)
+
+
+@pytest.mark.parametrize("scheme,order,dts", [("strang", 2, [0.1, 0.05, 0.025]),
+                                              ("yoshida4", 4, [0.2, 0.1, 0.05]),
+                                              ("suzuki4", 4, [0.4, 0.2, 0.1]),
+                                              ("yoshida6", 6, [0.4, 0.2, 0.1])])
+def test_moving_grid_convergence_order_vs_coherent_state(scheme, order, dts):
+    N, dq, T, x0, p0 = (64,), (0.3,), 2.0, 1.0, 0.5
+    errs = []
+    for dt in dts:
+        g = oracle.Grid(N, dq)
+        g.set_potential(oracle.POT_HARMONIC, [1.0, 0.0])
+        g.set_separable([("gauss", x0, p0, 1.0)], [x0], [p0])
+        g.propagate(round(T / dt), dt, scheme)
+        psi, q, _, _ = g.get_state()
+        exact, _, _ = coherent_state(g.qaxes(q)[0], T, 1.0, x0, p0)
+        errs.append(rel(psi, exact))
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(dts))
+    assert np.all(np.abs(slopes - order) < 0.3), (errs, slopes)
+
+
+# --------------------------------------------------------------------------
+# Invariants the paper proves (Sec. II.G): norm, reversibility, separability
+# --------------------------------------------------------------------------
+
+def atom_diatom_small():
+    P = inputs.ATOM_DIATOM
+    g = oracle.Grid((64, 48), dq=(0.32, 0.2), minv=(1 / P["mu"][0], 1 / P["mu"][1]))
+    g.set_potential(oracle.POT_ATOM_DIATOM, [P["Dm"], P["a"], P["re"], P["A"], P["beta"]])
+    rbar = oracle.morse_mean(P["Dm"], P["a"], P["re"], P["mu"][1])
+    g.set_separable([("gauss", P["R0"], P["P0"], P["sigma"]),
+                     ("morse", P["Dm"], P["a"], P["re"], P["mu"][1])],
+                    [P["R0"], rbar], [P["P0"], 0.0])
+    return g
+
+
+@pytest.mark.parametrize("split", [oracle.SPLIT_TVT, oracle.SPLIT_VTV])
+def test_norm_and_time_reversibility(split):
+    g = atom_diatom_small()
+    u0 = g.get_u()
+    _, q0, p0, _ = g.get_state()
+    n0 = np.sum(abs(u0) ** 2)
+    g.propagate(40, 2.0, "yoshida4", split)
+    u1 = g.get_u()
+    _, q1, p1, _ = g.get_state()
+    assert abs(np.sum(abs(u1) ** 2) / n0 - 1) < 1e-12
+    assert np.linalg.norm(q1 - q0) > 1e-2  # the grid actually moved
+    g.propagate(40, -2.0, "yoshida4", split)
+    u2 = g.get_u()
+    _, q2, p2, _ = g.get_state()
+    assert rel(u2, u0) < 1e-12
+    assert np.allclose(q2, q0, atol=1e-12, rtol=0) and np.allclose(p2, p0, atol=1e-11, rtol=0)
+
+
+def test_first_order_tv_is_not_reversible():
+    g = atom_diatom_small()
+    u0 = g.get_u()
+    g.propagate(40, 2.0, "strang", oracle.SPLIT_TV)
+    g.propagate(40, -2.0, "strang", oracle.SPLIT_TV)
+    assert rel(g.get_u(), u0) > 1e-6
+
+
+def test_separable_3d_equals_product_of_1d_runs():
+    P = inputs.HARMONIC3D
+    N = (16, 12, 20)
+    dq = (0.45, 0.5, 0.4)
+    om = np.array(P["omega"])
+    g3 = oracle.Grid(N, dq)
+    g3.set_potential(oracle.POT_HARMONIC, list(np.diag(om ** 2).ravel()) + [0, 0, 0])
+    g3.set_separable([("gauss", P["q0"][l], P["p0"][l], om[l] ** -0.5) for l in range(3)],
+                     P["q0"], P["p0"])
+    g3.propagate(50, 0.05, "suzuki4")
+    psi3, q3, p3, _ = g3.get_state()
+    facs, qs, ps = [], [], []
+    for l in range(3):
+        g1 = oracle.Grid((N[l],), (dq[l],))
+        g1.set_potential(oracle.POT_HARMONIC, [om[l] ** 2, 0.0])
+        g1.set_separable([("gauss", P["q0"][l], P["p0"][l], om[l] ** -0.5)], [P["q0"][l]], [P["p0"][l]])
+        g1.propagate(50, 0.05, "suzuki4")
+        psi1, q1, p1, _ = g1.get_state()
+        facs.append(psi1)
+        qs.append(q1[0])
+        ps.append(p1[0])
+    prod = np.multiply.outer(np.multiply.outer(facs[0], facs[1]), facs[2])
+    assert rel(psi3, prod) < 1e-12
+    assert np.allclose(q3, qs, atol=1e-13, rtol=0) and np.allclose(p3, ps, atol=1e-13, rtol=0)
+
+
+# --------------------------------------------------------------------------
+# Numbers the paper prints
+# --------------------------------------------------------------------------
+
+def duschinsky(K13):
+    P = inputs.DUSCHINSKY3D
+    g = oracle.Grid(P["N"], P["dq"], minv=P["omega"])
+    K = np.array(P["K"])
+    K[0, 2] = K[2, 0] = K13
+    g.set_potential(oracle.POT_HARMONIC, list(K.ravel()) + list(P["q0"]))
+    g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 3, [0, 0, 0], [0, 0, 0])
+    return g
+
+
+def test_initial_energy_of_the_harmonic_model():
+    # Sec. III.A, Fig. 4 caption: E0 = 140.389 n.u.; holds with K13 = +0.017.
+    n, E, mq, mp = duschinsky(+0.017).observables()
+    assert abs(n - 1) < 1e-9
+    assert abs(E - 140.389) < 6e-4
+    # Table I as printed (K13 = -0.017) gives 142.055 instead.
+    assert abs(duschinsky(-0.017).observables()[1] - 142.055) < 6e-4
+
+
+def test_overlap_harmonic_displaced_ground_state():
+    # Fig. 4 caption: phi0 = psi0 displaced by (-1, 1, 1) has <psi0|phi0> = 0.472.
+    P = inputs.DUSCHINSKY3D
+    g = oracle.Grid(P["N"], P["dq"])
+    g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 3, [0, 0, 0], [0, 0, 0])
+    a = g.get_u()
+    g.set_separable([("gauss", d, 0.0, 1.0) for d in (-1, 1, 1)], [0, 0, 0], [0, 0, 0])
+    b = g.get_u()
+    ov = np.vdot(a, b)
+    assert abs(ov.real - 0.472) < 5e-4 and abs(ov.imag) < 1e-14
+
+
+def test_overlap_scattering_packets():
+    # Fig. 7 caption: p0 = -3.0 instead of -3.56 gives |<psi0|phi0>| = 0.534
+    # (eq:general_GWP with sigma0^2 = 8, q0 = 24; grid of Fig. 5 caption).
+    N, rng1, rng2 = (128, 128), (-14.0, 14.0), (0.0, 48.0)
+    dq = ((rng1[1] - rng1[0]) / N[0], (rng2[1] - rng2[0]) / N[1])
+    g = oracle.Grid(N, dq, minv=(1.0, 1.5))
+    s0 = np.sqrt(8.0)
+    g.set_separable([("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.56, s0)], [0, 24], [0, -3.56])
+    a = g.get_u()
+    g.set_separable([("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.0, s0)], [0, 24], [0, -3.56])
+    b = g.get_u()
+    assert abs(abs(np.vdot(a, b)) - 0.534) < 5e-4
+
+
+# --------------------------------------------------------------------------
+# Composition coefficients, Morse ground state, regridding
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,stages,gmax", [
+    ("strang", 1, 1.0), ("yoshida4", 3, 1.7024), ("yoshida6", 9, 2.2971),
+    ("yoshida8", 27, 2.8309), ("yoshida10", 81, 3.3237), ("suzuki4", 5, 0.6580),
+    ("suzuki6", 25, 0.3239), ("suzuki8", 125, 0.1420), ("suzuki10", 625, 0.05845)])
+def test_composition_coefficients(name, stages, gmax):
+    g = oracle.scheme(name)
+    assert len(g) == stages
+    assert abs(g.sum() - 1) < 1e-13
+    assert np.array_equal(g, g[::-1])
+    assert abs(np.abs(g).max() - gmax) < 1e-4
+    order = 2 if name == "strang" else int(name[-2:] if name.endswith("10") else name[-1])
+    # order conditions of symmetric compositions of a symmetric 2nd-order method
+    for pw in range(3, order, 2):
+        assert abs(np.sum(g ** pw)) < 1e-10
+
+
+def test_morse_mean_closed_form():
+    P = inputs.ATOM_DIATOM
+    m = P["mu"][1]
+    lam = np.sqrt(2 * m * P["Dm"]) / P["a"]
+    # z = 2 lam e^{-a(r-re)} is Gamma(2 lam - 1)-distributed under |phi0|^2
+    exact = P["re"] - (digamma(2 * lam - 1) - np.log(2 * lam)) / P["a"]
+    assert abs(oracle.morse_mean(P["Dm"], P["a"], P["re"], m) - exact) < 1e-10
+
+
+def test_regrid_resamples_a_band_limited_packet():
+    g = oracle.Grid((64,), (0.3,))
+    G = Gauss1D(0.4, 0.7, 1.0)
+    qb, qa, p = np.array([0.0]), np.array([0.83]), np.array([0.7])
+    ub = G(g.qaxes(qb)[0]) * np.sqrt(0.3)
+    ua = G(g.qaxes(qa)[0]) * np.sqrt(0.3)
+    assert rel(g.regrid(ub, qb, p, qa), ua) < 1e-12
