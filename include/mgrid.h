@@ -1,0 +1,138 @@
+/* mgrid: GPU (sm_103a) moving-grid split-operator propagator for the
+ * time-dependent Schroedinger equation, after Choi & Vanicek,
+ * "A time-reversible integrator for the time-dependent Schroedinger
+ * equation on an adaptive grid" (arXiv:1909.06412).
+ *
+ * One context = one D-dimensional tensor-product grid (Sec. II.B,
+ * eq:multi_index_I, eq:x_I_definition) whose centre (q_t, p_t) moves with
+ * the wavepacket: inside every kinetic substep the q-centre advances by
+ * tau m^-1 <p> (eq:eom_qt_case_III_T), inside every potential substep the
+ * p-centre advances by -tau <dV/dq> (eq:eom_pt_solution_case_III_V).
+ * Substeps are composed symmetrically (eq:SO_TVT, eq:comp_TVT).
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: axis l has N_l points (even, 2 <= N_l <= 2048, only factors 2 and 3),
+ *    spacing dq_l > 0 and momentum spacing dp_l = 2 pi hbar / (N_l dq_l);
+ *    x_l^J = q_l + (j_l - N_l/2) dq_l and p_l^K = p_l + (k_l - N_l/2) dp_l.
+ *  - Arrays: row-major, last axis contiguous; complex values interleaved
+ *    (re, im); host arrays are always FP64.
+ *  - Device memory is owned by the caller (a torch tensor, say): the library
+ *    never allocates or frees device memory.  d_psi holds the scaled state
+ *    u^J = psi(x^J) sqrt(prod dq_l) (so sum |u|^2 is the norm of
+ *    eq:scalar_prod) as complex128 (MG_FP64) or complex64 (MG_FP32_MIXED).
+ *  - Work runs on the stream given at creation.  Entry points that return
+ *    data to the host synchronise that stream; the others only enqueue.
+ *  - Errors: every call returns an mg_status.  Device-side failures (barrier
+ *    timeout, non-finite norm, runaway grid centre) are recorded in a device
+ *    word and reported by the next synchronising call (mg_sync, mg_get_*).
+ *  - A context is not thread-safe; use one per stream.
+ */
+#ifndef MGRID_H
+#define MGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, unknown name) */
+  MG_ERR_UNSUPPORTED = -2, /* valid but not supported by this build (axis length, D) */
+  MG_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  MG_ERR_TIMEOUT = -4,     /* a grid-wide barrier in the persistent kernel timed out */
+  MG_ERR_NONFINITE = -5,   /* the norm or a reduction became non-finite */
+  MG_ERR_UNSTABLE = -6,    /* a grid centre jumped by more than 10 grid spans in one substep
+                              (Verlet instability of Sec. II.H, eq:verlet_stability_cond) */
+  MG_ERR_STATE = -7        /* call out of order (no potential or state set yet) */
+} mg_status;
+
+enum { MG_FP64 = 0, MG_FP32_MIXED = 1 };
+/* eq:SO_TVT (T half-steps around V), its V<->T exchange, and first-order
+ * eq:SO_TV (U_T U_V: the potential acts first). */
+enum { MG_TVT = 0, MG_VTV = 1, MG_TV = 2 };
+/* ADAPTIVE: q-centre moves with the <p> reduction (eq:eom_qt_case_III_T);
+ * ADAPTIVE_CENTRE_P: moves with the p-centre itself (eq:eom_qt_solution_case_III_T);
+ * FIXED: centres never move (the conventional split-operator method). */
+enum { MG_GRID_ADAPTIVE = 0, MG_GRID_ADAPTIVE_CENTRE_P = 1, MG_GRID_FIXED = 2 };
+/* Potentials (params layout):
+ *  HARMONIC        [K (D*D row-major, symmetric), c (D)]: V = 1/2 (x-c)^T K (x-c)
+ *  ATOM_DIATOM     D=2, axes (R, r), [Dm, a, re, A, beta]:
+ *                  V = Dm (1-e^{-a(r-re)})^2 + A e^{-beta(R-r/2)} + A e^{-beta(R+r/2)}
+ *  HENON_HEILES    [lambda]: V = sum x_l^2/2 + lambda sum_{l<D} (x_l^2 x_{l+1} - x_{l+1}^3/3)
+ *                  (Sec. III.C)
+ *  SECREST_JOHNSON D=2, [Dm, beta, alpha]: V = Dm (1-e^{-beta q1})^2 + e^{-alpha(q2-q1)}
+ *                  (eq:modified_secrest_johnson) */
+enum { MG_POT_HARMONIC = 0, MG_POT_ATOM_DIATOM = 1, MG_POT_HENON_HEILES = 2,
+       MG_POT_SECREST_JOHNSON = 3 };
+
+/* Device workspace the caller must provide for a grid (bytes, 256-aligned
+ * start required).  Returns 0 for an invalid or unsupported grid. */
+size_t mg_workspace_bytes(int D, const int64_t* N, int precision);
+
+/* Create a context (Sec. II.B grid; eq:KE_operator kinetic energy).
+ * minv: D*D row-major inverse mass matrix; only diagonal matrices are
+ * supported (MG_ERR_UNSUPPORTED otherwise).  d_psi: device buffer of
+ * prod(N) complex elements of the chosen precision.  d_work: device buffer of
+ * at least mg_workspace_bytes() bytes.  cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream).  The context keeps the pointers, not copies. */
+mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv,
+                    double hbar, int precision, void* d_psi, void* d_work, size_t work_bytes,
+                    void* cuda_stream);
+mg_status mg_destroy(mg_ctx* ctx);
+
+/* Select the potential (eq:hamiltonian); layouts above. */
+mg_status mg_set_potential(mg_ctx* ctx, int kind, const double* params, int nparams);
+
+/* Upload a physical wavefunction psi(x^J) (host, interleaved FP64,
+ * prod(N) complex values) sampled on the grid centred at (q, p), with time t.
+ * psi == NULL keeps the device state and only sets (q, p, t). */
+mg_status mg_set_state(mg_ctx* ctx, const double* psi, const double* q, const double* p, double t);
+
+/* Build a separable initial state on the grid centred at (q_ctr, p_ctr), t=0.
+ * Per axis l, kinds[l] and params[4*l .. 4*l+3]:
+ *   0 Gaussian (eq:general_GWP): [q0, p0, sigma, -]:
+ *     (pi sigma^2)^{-1/4} exp[-(x-q0)^2/(2 sigma^2) + i p0 (x-q0)/hbar]
+ *   1 Morse ground state [Dm, a, re, mass]: N z^{lam-1/2} e^{-z/2},
+ *     z = 2 lam e^{-a(x-re)}, lam = sqrt(2 mass Dm)/(a hbar). */
+mg_status mg_set_separable(mg_ctx* ctx, const int* kinds, const double* params,
+                           const double* q_ctr, const double* p_ctr);
+
+/* Propagate n_steps time steps dt (negative dt propagates backward) with a
+ * named symmetric composition (eq:comp_TVT): "strang" (second order),
+ * "yoshida4|6|8|10" (triple jump) or "suzuki4|6|8|10" (Suzuki fractal),
+ * applied to the split `split` with grid motion `grid_motion`.  All steps run
+ * in one persistent kernel launch on the context's stream. */
+mg_status mg_propagate(mg_ctx* ctx, int64_t n_steps, double dt, const char* scheme, int split,
+                       int grid_motion);
+
+/* Synchronise and read back: psi (physical psi(x^J), host FP64 interleaved,
+ * may be NULL), grid centres q, p (D doubles each, may be NULL) and time t. */
+mg_status mg_get_state(mg_ctx* ctx, double* psi, double* q, double* p, double* t);
+
+/* Synchronise and compute norm = sum |u|^2 (eq:scalar_prod), energy
+ * <T> + <V> (Sec. III.A), <q> and <p> (normalised by the norm).  Any output
+ * pointer may be NULL. */
+mg_status mg_get_observables(mg_ctx* ctx, double* norm, double* energy, double* mean_q,
+                             double* mean_p);
+
+/* Synchronise the context's stream and report any pending device status. */
+mg_status mg_sync(mg_ctx* ctx);
+
+/* Number of kernels this context has launched so far. */
+int64_t mg_kernel_launches(const mg_ctx* ctx);
+
+/* <x> under the Morse ground state above (host quadrature helper for
+ * choosing an initial grid centre). */
+double mg_morse_mean(double Dm, double a, double re, double mass, double hbar);
+
+const char* mg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -39,12 +39,71 @@ static const double TWO_PI = 6.283185307179586476925286766559;
 
 static int is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
+/* ------------------------------------------------------------------------ */
+/* Accurate phase factors                                                   */
+/* ------------------------------------------------------------------------ */
+/* The phases of eq:t_definition reach tens to hundreds of radians; a plain
+ * FP64 product loses ~1e-14 rad on such arguments, and those errors build up
+ * over thousands of substeps.  Phase arguments are therefore accumulated as
+ * unevaluated sums hi + lo (error-free products by fma, Dekker/Knuth
+ * two-sum) and reduced modulo 2 pi with a two-word 2 pi before cos/sin, so
+ * every factor e^{i theta} is correct to a few 1e-16 whatever |theta|. */
+typedef struct { double hi, lo; } dd;
+
+static const double TWO_PI_HI = 6.283185307179586232;      /* fl(2 pi)       */
+static const double TWO_PI_LO = 2.4492935982947064e-16;    /* 2 pi - fl(2 pi) */
+
+static dd two_sum(double a, double b) {
+  double s = a + b, bb = s - a;
+  return (dd){s, (a - (s - bb)) + (b - bb)};
+}
+static dd fast_two_sum(double a, double b) {
+  double s = a + b;
+  return (dd){s, b - (s - a)};
+}
+static dd dd_of_prod(double a, double b) {
+  double p = a * b;
+  return (dd){p, fma(a, b, -p)};
+}
+static dd dd_add(dd x, dd y) {
+  dd s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+static dd dd_mul(dd x, dd y) {
+  dd p = dd_of_prod(x.hi, y.hi);
+  p.lo += x.hi * y.lo + x.lo * y.hi;
+  return fast_two_sum(p.hi, p.lo);
+}
+static dd dd_mul_d(dd x, double b) {
+  dd p = dd_of_prod(x.hi, b);
+  p.lo += x.lo * b;
+  return fast_two_sum(p.hi, p.lo);
+}
+static dd dd_div_d(dd x, double b) {
+  double q1 = x.hi / b;
+  dd p = dd_of_prod(q1, b);
+  double r = ((x.hi - p.hi) - p.lo) + x.lo;
+  return fast_two_sum(q1, r / b);
+}
+/* e^{i theta} for theta = hi + lo. */
+static cplx expi(dd th) {
+  double k = nearbyint(th.hi / TWO_PI_HI);
+  dd kp = dd_of_prod(k, TWO_PI_HI);
+  double r = ((th.hi - kp.hi) - kp.lo) + th.lo - k * TWO_PI_LO;
+  return cos(r) + I * sin(r);
+}
+
 /* e^{sign 2 pi i m / n} with the integer m reduced modulo n first. */
 static cplx root_of_unity(int64_t m, int64_t n, int sign) {
   int64_t r = m % n;
   if (r < 0) r += n;
-  double a = TWO_PI * (double)r / (double)n;
-  return cos(a) + (double)sign * I * sin(a);
+  dd a = dd_add(dd_of_prod(TWO_PI_HI, (double)r), dd_of_prod(TWO_PI_LO, (double)r));
+  a = dd_div_d(a, (double)n);
+  if (sign < 0) { a.hi = -a.hi; a.lo = -a.lo; }
+  return expi(a);
 }
 
 int orc_dft1d_direct(int64_t n, const double* in, double* out, int sign) {
@@ -83,24 +142,34 @@ static void fft_radix2(int64_t n, cplx* x, int sign) {
   }
 }
 
-int orc_dft1d(int64_t n, double* xin, int sign) {
-  if (n <= 0 || (sign != 1 && sign != -1)) return -1;
-  cplx* x = (cplx*)xin;
+/* Unnormalised DFT of one line: radix-2 FFT or direct sum. */
+static int dft_line(int64_t n, cplx* x, int sign) {
   if (is_pow2(n)) {
     fft_radix2(n, x, sign);
-    double s = 1.0 / sqrt((double)n);
-    for (int64_t i = 0; i < n; ++i) x[i] *= s;
     return 0;
   }
   cplx* tmp = malloc(sizeof(cplx) * (size_t)n);
   if (!tmp) return -2;
-  orc_dft1d_direct(n, xin, (double*)tmp, sign);
+  for (int64_t k = 0; k < n; ++k) {
+    cplx acc = 0;
+    for (int64_t j = 0; j < n; ++j) acc += root_of_unity(k * j, n, sign) * x[j];
+    tmp[k] = acc;
+  }
   memcpy(x, tmp, sizeof(cplx) * (size_t)n);
   free(tmp);
   return 0;
 }
 
-/* Unitary DFT along every axis of a D-dimensional row-major array. */
+int orc_dft1d(int64_t n, double* xin, int sign) {
+  if (n <= 0 || (sign != 1 && sign != -1)) return -1;
+  cplx* x = (cplx*)xin;
+  int rc = dft_line(n, x, sign);
+  double s = 1.0 / sqrt((double)n);
+  for (int64_t i = 0; i < n; ++i) x[i] *= s;
+  return rc;
+}
+
+/* Unnormalised DFT along every axis of a D-dimensional row-major array. */
 static int dft_all_axes(const orc_ctx* c, cplx* a, int sign) {
   int64_t maxn = 0;
   for (int l = 0; l < c->D; ++l) maxn = c->N[l] > maxn ? c->N[l] : maxn;
@@ -114,7 +183,7 @@ static int dft_all_axes(const orc_ctx* c, cplx* a, int sign) {
       for (int64_t i = 0; i < stride; ++i) {
         cplx* base = a + o * n * stride + i;
         for (int64_t j = 0; j < n; ++j) line[j] = base[j * stride];
-        orc_dft1d(n, (double*)line, sign);
+        dft_line(n, line, sign);
         for (int64_t j = 0; j < n; ++j) base[j * stride] = line[j];
       }
     }
@@ -419,56 +488,57 @@ int orc_set_separable(orc_ctx* c, const int* kinds, const double* params, const 
  *               - pi hbar (j_l + k_l)].
  * The J-dependent part of t is applied before the DFT, the K-dependent and
  * constant parts after it; f~ = f^dagger reverses this. */
+/* scale: 0 = N^{-1/2} (the unitary f of eq:F_defintion), 1 = none, 2 = 1/N.
+ * Inside a kinetic substep the forward transform is left unscaled and the
+ * inverse divided by N: the two N^{-1/2} factors of f~ f applied as one exact
+ * (power-of-two N) or correctly rounded division, so that f~ f = 1
+ * (eq:F_inv_definition) holds without a systematic rounding bias. */
+static int apply_f_scaled(const orc_ctx* c, const double* q, const double* p, const double* in,
+                          double* out, int sign, int scale);
+
 int orc_apply_f(const orc_ctx* c, const double* q, const double* p, const double* in, double* out,
                 int sign) {
+  return apply_f_scaled(c, q, p, in, out, sign, 0);
+}
+
+static int apply_f_scaled(const orc_ctx* c, const double* q, const double* p, const double* in,
+                          double* out, int sign, int scale) {
   if (sign != 1 && sign != -1) return -1;
   const int D = c->D;
   const double hb = c->hbar;
   cplx* a = (cplx*)out;
   memcpy(a, in, sizeof(cplx) * (size_t)c->npts);
   int64_t idx[ORC_MAXD];
-  double cst = 0;
-  for (int l = 0; l < D; ++l)
-    cst += (p[l] - 0.5 * c->dp[l] * (double)c->N[l]) * (q[l] - 0.5 * c->dq[l] * (double)c->N[l]);
-  if (sign == -1) {
-    for (int64_t J = 0; J < c->npts; ++J) {
-      unflatten(c, J, idx);
-      double ph = 0, sg = 1;
-      for (int l = 0; l < D; ++l) {
-        ph += p[l] * (double)idx[l] * c->dq[l];
-        if (idx[l] & 1) sg = -sg;
+  /* constant part: sum_l (p_l - dp_l N_l/2)(q_l - dq_l N_l/2) */
+  dd cst = {0, 0};
+  for (int l = 0; l < D; ++l) {
+    dd pa = dd_add((dd){p[l], 0}, dd_mul_d((dd){c->dp[l], 0}, -0.5 * (double)c->N[l]));
+    dd qa = dd_add((dd){q[l], 0}, dd_mul_d((dd){c->dq[l], 0}, -0.5 * (double)c->N[l]));
+    cst = dd_add(cst, dd_mul(pa, qa));
+  }
+  /* J part: sum_l p_l j_l dq_l;  K part: cst + sum_l q_l k_l dp_l (then / hbar) */
+  for (int pass = 0; pass < 2; ++pass) {
+    const int jpart = (sign == -1) == (pass == 0);
+    if (pass == 1) {
+      dft_all_axes(c, a, sign);
+      const double nn = (double)c->npts, rs = 1.0 / sqrt(nn);
+      for (int64_t K = 0; K < c->npts; ++K) {
+        if (scale == 0) a[K] *= rs;
+        else if (scale == 2) a[K] = creal(a[K]) / nn + I * (cimag(a[K]) / nn);
       }
-      a[J] *= sg * cexp(-I * ph / hb);
     }
-    dft_all_axes(c, a, -1);
-    for (int64_t K = 0; K < c->npts; ++K) {
-      unflatten(c, K, idx);
-      double ph = cst, sg = 1;
+    for (int64_t I_ = 0; I_ < c->npts; ++I_) {
+      unflatten(c, I_, idx);
+      dd ph = jpart ? (dd){0, 0} : cst;
+      double sg = 1;
       for (int l = 0; l < D; ++l) {
-        ph += q[l] * (double)idx[l] * c->dp[l];
+        dd f = jpart ? dd_of_prod(p[l], c->dq[l]) : dd_of_prod(q[l], c->dp[l]);
+        ph = dd_add(ph, dd_mul_d(f, (double)idx[l]));
         if (idx[l] & 1) sg = -sg;
       }
-      a[K] *= sg * cexp(-I * ph / hb);
-    }
-  } else {
-    for (int64_t K = 0; K < c->npts; ++K) {
-      unflatten(c, K, idx);
-      double ph = cst, sg = 1;
-      for (int l = 0; l < D; ++l) {
-        ph += q[l] * (double)idx[l] * c->dp[l];
-        if (idx[l] & 1) sg = -sg;
-      }
-      a[K] *= sg * cexp(I * ph / hb);
-    }
-    dft_all_axes(c, a, 1);
-    for (int64_t J = 0; J < c->npts; ++J) {
-      unflatten(c, J, idx);
-      double ph = 0, sg = 1;
-      for (int l = 0; l < D; ++l) {
-        ph += p[l] * (double)idx[l] * c->dq[l];
-        if (idx[l] & 1) sg = -sg;
-      }
-      a[J] *= sg * cexp(I * ph / hb);
+      ph = dd_div_d(ph, hb);
+      if (sign == -1) { ph.hi = -ph.hi; ph.lo = -ph.lo; }
+      a[I_] *= sg * expi(ph);
     }
   }
   return 0;
@@ -538,7 +608,7 @@ int orc_substep_T(orc_ctx* c, double tau, int grid_motion) {
   const int D = c->D;
   cplx* phi = malloc(sizeof(cplx) * (size_t)c->npts);
   if (!phi) return -2;
-  orc_apply_f(c, c->q, c->p, (const double*)c->u, (double*)phi, -1);
+  apply_f_scaled(c, c->q, c->p, (const double*)c->u, (double*)phi, -1, 1);
   int64_t k[ORC_MAXD];
   double pk[ORC_MAXD], ps[ORC_MAXD] = {0}, n = 0;
   for (int64_t K = 0; K < c->npts; ++K) {
@@ -562,7 +632,7 @@ int orc_substep_T(orc_ctx* c, double tau, int grid_motion) {
     ppoint(c, c->p, k, pk);
     phi[K] *= cexp(-I * tau * kinetic(c, pk) / c->hbar);
   }
-  orc_apply_f(c, qn, c->p, (const double*)phi, (double*)c->u, 1);
+  apply_f_scaled(c, qn, c->p, (const double*)phi, (double*)c->u, 1, 2);
   memcpy(c->q, qn, sizeof(double) * (size_t)D);
   free(phi);
   return 0;

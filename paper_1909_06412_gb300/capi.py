@@ -1,0 +1,187 @@
+"""ctypes binding of the C-ABI in ``include/mgrid.h`` (same names), plus a thin
+``Propagator`` that owns torch device buffers and forwards every call.
+
+Only argument marshalling happens here; every step of the propagation runs in
+the CUDA kernels of ``lib/libmgrid.so``.  Loading fails with an ImportError if
+the library is missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmgrid.so")
+
+MG_OK, MG_ERR_ARG, MG_ERR_UNSUPPORTED, MG_ERR_CUDA = 0, -1, -2, -3
+MG_ERR_TIMEOUT, MG_ERR_NONFINITE, MG_ERR_UNSTABLE, MG_ERR_STATE = -4, -5, -6, -7
+MG_FP64, MG_FP32_MIXED = 0, 1
+MG_TVT, MG_VTV, MG_TV = 0, 1, 2
+MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED = 0, 1, 2
+MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON = 0, 1, 2, 3
+
+__all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "MgError", "lib", "mg_workspace_bytes",
+                                                        "mg_morse_mean"]
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        L.mg_workspace_bytes.argtypes = [i32, vp, i32]
+        L.mg_workspace_bytes.restype = sz
+        L.mg_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, d, i32, vp, vp, sz, vp]
+        L.mg_destroy.argtypes = [vp]
+        L.mg_set_potential.argtypes = [vp, i32, vp, i32]
+        L.mg_set_state.argtypes = [vp, vp, vp, vp, d]
+        L.mg_set_separable.argtypes = [vp, vp, vp, vp, vp]
+        L.mg_propagate.argtypes = [vp, i64, d, ctypes.c_char_p, i32, i32]
+        L.mg_get_state.argtypes = [vp, vp, vp, vp, vp]
+        L.mg_get_observables.argtypes = [vp, vp, vp, vp, vp]
+        L.mg_sync.argtypes = [vp]
+        L.mg_kernel_launches.argtypes = [vp]
+        L.mg_kernel_launches.restype = i64
+        L.mg_morse_mean.argtypes = [d, d, d, d, d]
+        L.mg_morse_mean.restype = d
+        L.mg_status_string.argtypes = [i32]
+        L.mg_status_string.restype = ctypes.c_char_p
+        for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+class MgError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {lib().mg_status_string(code).decode()} ({code})")
+
+
+def _check(code, what):
+    if code != MG_OK:
+        raise MgError(code, what)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(x, n=None):
+    a = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def mg_workspace_bytes(N, precision=MG_FP64):
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    return int(lib().mg_workspace_bytes(len(n), _ptr(n), precision))
+
+
+def mg_morse_mean(Dm, a, re, mass, hbar=1.0):
+    return float(lib().mg_morse_mean(Dm, a, re, mass, hbar))
+
+
+class Propagator:
+    """One grid context whose state and workspace live in torch CUDA tensors."""
+
+    def __init__(self, N, dq, minv=None, hbar=1.0, precision=MG_FP64, device=None, stream=None):
+        import torch
+
+        self.torch = torch
+        self.N = tuple(int(v) for v in N)
+        self.D = len(self.N)
+        self.npts = int(np.prod(self.N))
+        self.dq = _f64(dq, self.D)
+        if minv is None:
+            minv = np.ones(self.D)
+        minv = np.asarray(minv, dtype=np.float64)
+        self.minv = _f64(np.diag(minv) if minv.ndim == 1 else minv, self.D * self.D)
+        self.hbar = float(hbar)
+        self.precision = precision
+        self.device = torch.device(device or "cuda")
+        ws = mg_workspace_bytes(self.N, precision)
+        if ws == 0:
+            raise MgError(MG_ERR_UNSUPPORTED, "mg_workspace_bytes")
+        fdt = torch.float64 if precision == MG_FP64 else torch.float32
+        self.psi = torch.zeros(2 * self.npts, dtype=fdt, device=self.device)
+        self.work = torch.zeros(ws, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = np.ascontiguousarray(self.N, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib().mg_create(ctypes.byref(h), self.D, _ptr(n), _ptr(self.dq), _ptr(self.minv), self.hbar,
+                             precision, ctypes.c_void_p(self.psi.data_ptr()), ctypes.c_void_p(self.work.data_ptr()),
+                             ws, ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, "mg_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_potential(self, kind, params):
+        p = _f64(params)
+        _check(lib().mg_set_potential(self._h, kind, _ptr(p), p.size), "mg_set_potential")
+
+    def set_state(self, psi, q, p, t=0.0):
+        q, p = _f64(q, self.D), _f64(p, self.D)
+        if psi is None:
+            ptr = None
+        else:
+            arr = np.ascontiguousarray(psi, dtype=np.complex128).reshape(self.N)
+            ptr = _ptr(arr)
+        _check(lib().mg_set_state(self._h, ptr, _ptr(q), _ptr(p), float(t)), "mg_set_state")
+
+    def set_separable(self, factors, q_ctr, p_ctr):
+        """factors: per axis ('gauss', q0, p0, sigma) or ('morse', Dm, a, re, mass)."""
+        kinds = np.zeros(self.D, dtype=np.int32)
+        params = np.zeros((self.D, 4))
+        for l, f in enumerate(factors):
+            kinds[l] = {"gauss": 0, "morse": 1}[f[0]]
+            params[l, : len(f) - 1] = f[1:]
+        q, p = _f64(q_ctr, self.D), _f64(p_ctr, self.D)
+        _check(lib().mg_set_separable(self._h, _ptr(kinds), _ptr(params), _ptr(q), _ptr(p)), "mg_set_separable")
+
+    def propagate(self, n_steps, dt, scheme="strang", split=MG_TVT, grid_motion=MG_GRID_ADAPTIVE):
+        rc = lib().mg_propagate(self._h, int(n_steps), float(dt), scheme.encode(), split, grid_motion)
+        _check(rc, "mg_propagate")
+
+    def sync(self):
+        _check(lib().mg_sync(self._h), "mg_sync")
+
+    def get_state(self, want_psi=True):
+        psi = np.empty(self.N, dtype=np.complex128) if want_psi else None
+        q, p, t = np.empty(self.D), np.empty(self.D), np.zeros(1)
+        rc = lib().mg_get_state(self._h, _ptr(psi) if want_psi else None, _ptr(q), _ptr(p), _ptr(t))
+        _check(rc, "mg_get_state")
+        return psi, q, p, float(t[0])
+
+    def observables(self):
+        n, e = np.zeros(1), np.zeros(1)
+        mq, mp = np.empty(self.D), np.empty(self.D)
+        _check(lib().mg_get_observables(self._h, _ptr(n), _ptr(e), _ptr(mq), _ptr(mp)), "mg_get_observables")
+        return float(n[0]), float(e[0]), mq, mp
+
+    @property
+    def launches(self):
+        return int(lib().mg_kernel_launches(self._h))

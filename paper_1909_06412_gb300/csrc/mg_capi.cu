@@ -1,0 +1,650 @@
+// Host side of the C-ABI declared in include/mgrid.h: validation, planning of
+// the axis passes, workspace layout, host-side state preparation (initial
+// wavepackets, composition coefficients) and kernel launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_plan.h"
+#include "mgrid.h"
+
+namespace mgk {
+void* propagate_kernel(int prec, int kind);
+void* obs_kernel(int prec, int kind);
+void* init_tables_kernel();
+void* obs_tables_kernel();
+}  // namespace mgk
+
+using namespace mgk;
+
+namespace {
+
+constexpr int MAXBLOCKS = 2048;
+constexpr int RESIDENT_CAP = 96 * 1024;  // bytes per smem region when tiles stay resident
+constexpr int CHUNK_REGION = 64 * 1024;  // bytes per smem region otherwise
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, scratch, total;
+};
+
+Layout layout_for(int D, const int64_t* N) {
+  int64_t npts = 1, tt = 0;
+  for (int l = 0; l < D; ++l) {
+    npts *= N[l];
+    tt += N[l];
+  }
+  Layout L{};
+  size_t o = 0;
+  auto put = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.ctrl = put(32 * sizeof(double));
+  L.bar = put(64 * sizeof(unsigned));
+  L.status = put(sizeof(int));
+  L.part = put(2ull * MAXBLOCKS * PSTRIDE * sizeof(double));
+  L.tw = put(tt * sizeof(double2));
+  L.tabA = put(tt * sizeof(double2));
+  L.tabAi = put(tt * sizeof(double2));
+  L.tabK = put(tt * sizeof(double2));
+  L.tabV = put((size_t)NVCOL * tt * sizeof(double));
+  L.tabC = put(tt * sizeof(double));
+  L.tabE = put(tt * sizeof(double));
+  L.gamma = put(MAX_STAGES * sizeof(double));
+  L.scratch = put((size_t)npts * sizeof(double2));
+  L.total = o;
+  return L;
+}
+
+// Axis length check: even, 2..MAXN, only prime factors 2 and 3.
+bool axis_supported(int64_t n) {
+  if (n < 2 || n > MAXN || n % 2) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+void radix_plan(int n, AxisPlan& ax) {
+  int c2 = 0, c3 = 0;
+  while (n % 2 == 0) { n /= 2; ++c2; }
+  while (n % 3 == 0) { n /= 3; ++c3; }
+  ax.nrad = 0;
+  while (c2 >= 3) { ax.rad[ax.nrad++] = 8; c2 -= 3; }
+  if (c2 == 2) ax.rad[ax.nrad++] = 4;
+  if (c2 == 1) ax.rad[ax.nrad++] = 2;
+  for (int i = 0; i < c3; ++i) ax.rad[ax.nrad++] = 3;
+}
+
+size_t smem_for(const Plan& P) {
+  const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
+  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  size_t s = 3 * r16(vs * P.maxn) + r16(sizeof(double) * NVCOL * P.tab_total) +
+             2 * r16(sizeof(double) * P.tab_total) + r16(sizeof(double) * (THREADS / 32) * PSTRIDE) +
+             r16(sizeof(double) * PSTRIDE) + 2 * r16((size_t)P.region_bytes);
+  return s;
+}
+
+// Tile and chunk sizes for a given grid size of the persistent kernel.
+void tile_plan(Plan& P) {
+  const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
+  const int D = P.D;
+  int64_t need_res = 0, need_min = 0;
+  for (int l = 0; l < D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    const bool contig = (l == D - 1);
+    ax.W = contig ? 1 : (P.prec == 0 ? 2 : (ax.stride % 4 == 0 ? 4 : 2));
+    if (!contig && ax.W > ax.stride) ax.W = (int)ax.stride;
+    const int64_t lines = P.npts / ax.n;
+    ax.ntiles = lines / ax.W;
+    const int64_t tile_bytes = (int64_t)ax.W * ax.n * vs;
+    need_min = std::max(need_min, tile_bytes);
+    if (l == 0 || l == D - 1) {
+      const int64_t mine = (ax.ntiles + P.nblocks - 1) / P.nblocks;
+      need_res = std::max(need_res, mine * tile_bytes);
+    }
+  }
+  P.resident = need_res <= RESIDENT_CAP;
+  int64_t region = P.resident ? std::max(need_res, need_min) : std::max<int64_t>(CHUNK_REGION, need_min);
+  P.region_bytes = (int)((region + 15) & ~int64_t(15));
+  for (int l = 0; l < D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    const int64_t tile_bytes = (int64_t)ax.W * ax.n * vs;
+    ax.tpc = (int)std::max<int64_t>(1, P.region_bytes / tile_bytes);
+  }
+  P.smem_bytes = (int)smem_for(P);
+}
+
+// ---- composition coefficients (eq:comp_TVT; Yoshida 1990 triple jump,
+// ---- Suzuki 1990 fractal), built by recursion on the order -----------------
+
+bool scheme_coeffs(const char* name, std::vector<double>& g) {
+  if (!name) return false;
+  std::string s(name);
+  int family = -1, order = 0;
+  if (s == "strang") { family = 0; order = 2; }
+  else if (s.rfind("yoshida", 0) == 0) { family = 1; order = std::atoi(s.c_str() + 7); }
+  else if (s.rfind("suzuki", 0) == 0) { family = 2; order = std::atoi(s.c_str() + 6); }
+  if (family < 0 || order < 2 || order > 10 || order % 2) return false;
+  g.assign(1, 1.0);
+  for (int k = 1; 2 * k < order; ++k) {
+    // raise the order from 2k to 2k+2
+    const double e = 1.0 / (2 * k + 1);
+    std::vector<double> w;
+    if (family == 1) {
+      const double a = 1.0 / (2.0 - std::pow(2.0, e));
+      w = {a, 1.0 - 2.0 * a, a};
+    } else {
+      const double a = 1.0 / (4.0 - std::pow(4.0, e));
+      w = {a, a, 1.0 - 4.0 * a, a, a};
+    }
+    std::vector<double> next;
+    for (double wi : w)
+      for (double gi : g) next.push_back(wi * gi);
+    g.swap(next);
+  }
+  return (int)g.size() <= MAX_STAGES;
+}
+
+// ---- digamma by recurrence + asymptotic series (Abramowitz & Stegun 6.3.5,
+// ---- 6.3.18) for the Morse-state mean ------------------------------------------
+
+double digamma(double x) {
+  double r = 0;
+  while (x < 12.0) {
+    r -= 1.0 / x;
+    x += 1.0;
+  }
+  const double i2 = 1.0 / (x * x);
+  return r + std::log(x) - 0.5 / x -
+         i2 * (1.0 / 12 - i2 * (1.0 / 120 - i2 * (1.0 / 252 - i2 * (1.0 / 240 - i2 / 132))));
+}
+
+}  // namespace
+
+struct mg_ctx {
+  Plan P;
+  Bufs B;
+  Layout L;
+  cudaStream_t stream;
+  void* d_work;
+  size_t work_bytes;
+  double q[MAXD], p[MAXD], t;
+  bool pot_set, state_set;
+  int64_t launches;
+  std::vector<double> host;  // staging for psi
+  std::vector<double> gam;
+  double ctrl[32];
+};
+
+namespace {
+
+mg_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? MG_OK : MG_ERR_CUDA; }
+
+mg_status upload_ctrl(mg_ctx* c) {
+  for (int a = 0; a < MAXD; ++a) {
+    c->ctrl[a] = a < c->P.D ? c->q[a] : 0.0;
+    c->ctrl[8 + a] = a < c->P.D ? c->p[a] : 0.0;
+  }
+  c->ctrl[16] = c->t;
+  return cuda_ok(cudaMemcpyAsync(c->B.ctrl, c->ctrl, 17 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+}
+
+mg_status launch_plain(mg_ctx* c, void* fn, void** args, size_t smem) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return MG_ERR_CUDA;
+  }
+  cudaError_t e = cudaLaunchKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, smem, c->stream);
+  c->launches++;
+  return cuda_ok(e);
+}
+
+mg_status init_tables(mg_ctx* c) {
+  void* args[] = {&c->P, &c->B};
+  return launch_plain(c, init_tables_kernel(), args, 0);
+}
+
+mg_status read_status(mg_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return MG_ERR_CUDA;
+  int st = 0;
+  e = cudaMemcpy(&st, c->B.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return MG_ERR_CUDA;
+  if (st != 0) {
+    int zero = 0;
+    cudaMemcpy(c->B.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return (mg_status)st;
+  }
+  return MG_OK;
+}
+
+double sqrt_cell(const Plan& P) {
+  double v = 1;
+  for (int l = 0; l < P.D; ++l) v *= P.dq[l];
+  return std::sqrt(v);
+}
+
+// Copy the host FP64 scaled state into d_psi (converting to the storage type).
+mg_status upload_u(mg_ctx* c) {
+  const size_t n = (size_t)c->P.npts;
+  if (c->P.prec == 0)
+    return cuda_ok(cudaMemcpyAsync(c->B.psi, c->host.data(), n * sizeof(double2), cudaMemcpyHostToDevice,
+                                   c->stream));
+  std::vector<float> f(2 * n);
+  for (size_t i = 0; i < 2 * n; ++i) f[i] = (float)c->host[i];
+  mg_status s = cuda_ok(cudaMemcpyAsync(c->B.psi, f.data(), n * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mg_workspace_bytes(int D, const int64_t* N, int precision) {
+  if (D < 1 || D > MAXD || !N || (precision != MG_FP64 && precision != MG_FP32_MIXED)) return 0;
+  for (int l = 0; l < D; ++l)
+    if (!axis_supported(N[l])) return 0;
+  return layout_for(D, N).total;
+}
+
+mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv, double hbar,
+                    int precision, void* d_psi, void* d_work, size_t work_bytes, void* cuda_stream) {
+  if (!out || !N || !dq || !minv || !d_psi || !d_work) return MG_ERR_ARG;
+  *out = nullptr;
+  if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar)) return MG_ERR_ARG;
+  if (precision != MG_FP64 && precision != MG_FP32_MIXED) return MG_ERR_ARG;
+  if (precision != MG_FP64) return MG_ERR_UNSUPPORTED;
+  for (int l = 0; l < D; ++l) {
+    if (N[l] < 2 || N[l] % 2) return MG_ERR_ARG;
+    if (!(dq[l] > 0) || !std::isfinite(dq[l])) return MG_ERR_ARG;
+    if (!axis_supported(N[l])) return MG_ERR_UNSUPPORTED;
+  }
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      const double v = minv[a * D + b];
+      if (!std::isfinite(v)) return MG_ERR_ARG;
+      if (a != b && v != 0.0) return MG_ERR_UNSUPPORTED;
+      if (a == b && !(v > 0)) return MG_ERR_ARG;
+    }
+  if (((uintptr_t)d_work & 255) || ((uintptr_t)d_psi & 15)) return MG_ERR_ARG;
+  Layout L = layout_for(D, N);
+  if (work_bytes < L.total) return MG_ERR_ARG;
+
+  mg_ctx* c = new mg_ctx();
+  std::memset(&c->P, 0, sizeof(Plan));
+  Plan& P = c->P;
+  P.D = D;
+  P.prec = precision;
+  P.hbar = hbar;
+  P.npts = 1;
+  P.maxn = 0;
+  P.tab_total = 0;
+  P.pot_kind = -1;
+  for (int l = 0; l < D; ++l) P.npts *= N[l];
+  for (int l = D - 1; l >= 0; --l) {
+    AxisPlan& ax = P.ax[l];
+    ax.n = (int)N[l];
+    ax.stride = (l == D - 1) ? 1 : P.ax[l + 1].stride * N[l + 1];
+  }
+  for (int l = 0; l < D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    P.N[l] = N[l];
+    P.dq[l] = dq[l];
+    P.dp[l] = 2.0 * M_PI * hbar / ((double)N[l] * dq[l]);
+    P.minv[l] = minv[l * D + l];
+    ax.outer = P.npts / (ax.n * ax.stride);
+    ax.toff = P.tab_total;
+    P.tab_total += ax.n;
+    P.maxn = std::max(P.maxn, ax.n);
+    radix_plan(ax.n, ax);
+  }
+  // grid of the persistent kernel: one CTA per SM (all co-resident)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return MG_ERR_CUDA;
+  }
+  int per_sm = 1;
+  if (const char* e = std::getenv("MG_BLOCKS_PER_SM")) per_sm = std::max(1, std::atoi(e));
+  P.nblocks = std::min(MAXBLOCKS, sms * per_sm);
+  tile_plan(P);
+  for (int kind = 0; kind < 4; ++kind) {
+    void* fn = propagate_kernel(P.prec, kind);
+    if (P.smem_bytes > 48 * 1024)
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, THREADS, P.smem_bytes) != cudaSuccess || occ < 1) {
+      delete c;
+      return MG_ERR_UNSUPPORTED;
+    }
+    if (occ * sms < P.nblocks) {
+      P.nblocks = occ * sms;
+      tile_plan(P);
+    }
+  }
+
+  c->L = L;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->d_work = d_work;
+  c->work_bytes = work_bytes;
+  char* w = (char*)d_work;
+  Bufs& B = c->B;
+  B.psi = d_psi;
+  B.ctrl = (double*)(w + L.ctrl);
+  B.bar = (unsigned*)(w + L.bar);
+  B.status = (int*)(w + L.status);
+  B.part = (double*)(w + L.part);
+  B.tw = (double2*)(w + L.tw);
+  B.tabA = (double2*)(w + L.tabA);
+  B.tabAi = (double2*)(w + L.tabAi);
+  B.tabK = (double2*)(w + L.tabK);
+  B.tabV = (double*)(w + L.tabV);
+  B.tabC = (double*)(w + L.tabC);
+  B.tabE = (double*)(w + L.tabE);
+  B.gamma = (const double*)(w + L.gamma);
+  B.scratch = (double2*)(w + L.scratch);
+
+  // static tables: twiddles e^{-2 pi i m/N_l} and k - N_l/2
+  std::vector<double> tw(2 * P.tab_total), kc(P.tab_total);
+  for (int l = 0; l < D; ++l) {
+    const int n = P.ax[l].n;
+    for (int m = 0; m < n; ++m) {
+      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
+      tw[2 * (P.ax[l].toff + m)] = (double)std::cos(ang);
+      tw[2 * (P.ax[l].toff + m) + 1] = -(double)std::sin(ang);
+      kc[P.ax[l].toff + m] = (double)(m - n / 2);
+    }
+  }
+  mg_status s = cuda_ok(cudaMemsetAsync(d_work, 0, L.scratch, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tabC, kc.data(), kc.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s != MG_OK) {
+    delete c;
+    return s;
+  }
+  for (int a = 0; a < MAXD; ++a) c->q[a] = c->p[a] = 0.0;
+  c->t = 0;
+  c->pot_set = c->state_set = false;
+  c->launches = 0;
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_ctx* ctx) {
+  if (!ctx) return MG_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+  return MG_OK;
+}
+
+mg_status mg_set_potential(mg_ctx* c, int kind, const double* params, int nparams) {
+  if (!c || (!params && nparams > 0)) return MG_ERR_ARG;
+  const int D = c->P.D;
+  int need;
+  switch (kind) {
+    case MG_POT_HARMONIC: need = D * D + D; break;
+    case MG_POT_ATOM_DIATOM: need = 5; if (D != 2) return MG_ERR_ARG; break;
+    case MG_POT_HENON_HEILES: need = 1; break;
+    case MG_POT_SECREST_JOHNSON: need = 3; if (D != 2) return MG_ERR_ARG; break;
+    default: return MG_ERR_ARG;
+  }
+  if (nparams != need) return MG_ERR_ARG;
+  for (int i = 0; i < nparams; ++i)
+    if (!std::isfinite(params[i])) return MG_ERR_ARG;
+  c->P.pot_kind = kind;
+  c->P.pot_general = 0;
+  std::memset(c->P.pot, 0, sizeof(c->P.pot));
+  std::memcpy(c->P.pot, params, sizeof(double) * nparams);
+  if (kind == MG_POT_HARMONIC)
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        if (params[a * D + b] != params[b * D + a]) return MG_ERR_ARG;
+        if (a != b && params[a * D + b] != 0.0) c->P.pot_general = 1;
+      }
+  c->pot_set = true;
+  return MG_OK;
+}
+
+mg_status mg_set_state(mg_ctx* c, const double* psi, const double* q, const double* p, double t) {
+  if (!c || !q || !p || !std::isfinite(t)) return MG_ERR_ARG;
+  for (int a = 0; a < c->P.D; ++a)
+    if (!std::isfinite(q[a]) || !std::isfinite(p[a])) return MG_ERR_ARG;
+  mg_status s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s != MG_OK) return s;
+  if (psi) {
+    const size_t n = (size_t)c->P.npts;
+    const double sc = sqrt_cell(c->P);
+    c->host.resize(2 * n);
+    for (size_t i = 0; i < 2 * n; ++i) c->host[i] = psi[i] * sc;
+    s = upload_u(c);
+    if (s != MG_OK) return s;
+  } else if (!c->state_set) {
+    return MG_ERR_STATE;
+  }
+  for (int a = 0; a < c->P.D; ++a) {
+    c->q[a] = q[a];
+    c->p[a] = p[a];
+  }
+  c->t = t;
+  s = upload_ctrl(c);
+  if (s == MG_OK) s = init_tables(c);
+  if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s == MG_OK) c->state_set = true;
+  return s;
+}
+
+double mg_morse_mean(double Dm, double a, double re, double mass, double hbar) {
+  // <x> = re - (digamma(2 lam - 1) - ln(2 lam)) / a: z = 2 lam e^{-a(x - re)}
+  // is Gamma(2 lam - 1)-distributed under |phi0|^2.
+  const double lam = std::sqrt(2.0 * mass * Dm) / (a * hbar);
+  if (!(lam > 0.5)) return NAN;
+  return re - (digamma(2.0 * lam - 1.0) - std::log(2.0 * lam)) / a;
+}
+
+mg_status mg_set_separable(mg_ctx* c, const int* kinds, const double* params, const double* q_ctr,
+                           const double* p_ctr) {
+  if (!c || !kinds || !params || !q_ctr || !p_ctr) return MG_ERR_ARG;
+  const Plan& P = c->P;
+  const int D = P.D;
+  std::vector<std::vector<double>> fac(D);  // per-axis complex samples (re, im)
+  for (int l = 0; l < D; ++l) {
+    const double* w = params + 4 * l;
+    const int n = (int)P.N[l];
+    fac[l].resize(2 * n);
+    for (int j = 0; j < n; ++j) {
+      const double x = q_ctr[l] + (j - n / 2) * P.dq[l];
+      double re, im;
+      if (kinds[l] == 0) {
+        const double q0 = w[0], p0 = w[1], sg = w[2];
+        if (!(sg > 0)) return MG_ERR_ARG;
+        const double d = x - q0;
+        const double amp = std::pow(M_PI * sg * sg, -0.25) * std::exp(-d * d / (2.0 * sg * sg));
+        const double ph = p0 * d / P.hbar;
+        re = amp * std::cos(ph);
+        im = amp * std::sin(ph);
+      } else if (kinds[l] == 1) {
+        const double Dm = w[0], aa = w[1], re0 = w[2], mass = w[3];
+        const double lam = std::sqrt(2.0 * mass * Dm) / (aa * P.hbar);
+        if (!(lam > 0.5) || !(aa > 0)) return MG_ERR_ARG;
+        const double z = 2.0 * lam * std::exp(-aa * (x - re0));
+        const double lg = (lam - 0.5) * std::log(z) - 0.5 * z + 0.5 * (std::log(aa) - std::lgamma(2.0 * lam - 1.0));
+        re = std::exp(lg);
+        im = 0.0;
+      } else {
+        return MG_ERR_ARG;
+      }
+      fac[l][2 * j] = re;
+      fac[l][2 * j + 1] = im;
+    }
+  }
+  const size_t n = (size_t)P.npts;
+  const double sc = sqrt_cell(P);
+  mg_status s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s != MG_OK) return s;
+  c->host.resize(2 * n);
+  for (size_t J = 0; J < n; ++J) {
+    size_t rem = J;
+    double re = sc, im = 0.0;
+    for (int l = D - 1; l >= 0; --l) {
+      const size_t j = rem % (size_t)P.N[l];
+      rem /= (size_t)P.N[l];
+      const double fr = fac[l][2 * j], fi = fac[l][2 * j + 1];
+      const double nr = re * fr - im * fi;
+      im = re * fi + im * fr;
+      re = nr;
+    }
+    c->host[2 * J] = re;
+    c->host[2 * J + 1] = im;
+  }
+  s = upload_u(c);
+  if (s != MG_OK) return s;
+  for (int a = 0; a < D; ++a) {
+    c->q[a] = q_ctr[a];
+    c->p[a] = p_ctr[a];
+  }
+  c->t = 0;
+  s = upload_ctrl(c);
+  if (s == MG_OK) s = init_tables(c);
+  if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s == MG_OK) c->state_set = true;
+  return s;
+}
+
+mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme, int split, int grid_motion) {
+  if (!c || n_steps < 0 || !std::isfinite(dt)) return MG_ERR_ARG;
+  if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
+    return MG_ERR_ARG;
+  if (!scheme_coeffs(scheme, c->gam)) return MG_ERR_ARG;
+  if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
+  if (n_steps == 0) return MG_OK;
+  Run R{};
+  R.n_steps = n_steps;
+  R.S = (int)c->gam.size();
+  R.dt = dt;
+  R.split = split;
+  R.motion = grid_motion;
+  R.lead_v = split != MG_TVT;
+  R.n_units = (split == MG_TVT) ? n_steps * R.S + 1 : n_steps * R.S;
+  mg_status s = cuda_ok(cudaMemcpyAsync((void*)c->B.gamma, c->gam.data(), c->gam.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
+  if (s != MG_OK) return s;
+  void* fn = propagate_kernel(c->P.prec, c->P.pot_kind);
+  if (!fn) return MG_ERR_UNSUPPORTED;
+  if (c->P.smem_bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->P.smem_bytes) != cudaSuccess)
+    return MG_ERR_CUDA;
+  void* args[] = {&c->P, &c->B, &R};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, c->P.smem_bytes, c->stream);
+  c->launches++;
+  if (e != cudaSuccess) return MG_ERR_CUDA;
+  c->t += (double)n_steps * dt;
+  return MG_OK;
+}
+
+mg_status mg_sync(mg_ctx* c) {
+  if (!c) return MG_ERR_ARG;
+  return read_status(c);
+}
+
+mg_status mg_get_state(mg_ctx* c, double* psi, double* q, double* p, double* t) {
+  if (!c) return MG_ERR_ARG;
+  if (!c->state_set) return MG_ERR_STATE;
+  mg_status s = read_status(c);
+  if (s != MG_OK) return s;
+  const int D = c->P.D;
+  double ctrl[17];
+  if (cudaMemcpy(ctrl, c->B.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+  for (int a = 0; a < D; ++a) {
+    c->q[a] = ctrl[a];
+    c->p[a] = ctrl[8 + a];
+    if (q) q[a] = ctrl[a];
+    if (p) p[a] = ctrl[8 + a];
+  }
+  if (t) *t = c->t;
+  if (psi) {
+    const size_t n = (size_t)c->P.npts;
+    const double sc = 1.0 / sqrt_cell(c->P);
+    if (c->P.prec == 0) {
+      if (cudaMemcpy(psi, c->B.psi, n * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+      for (size_t i = 0; i < 2 * n; ++i) psi[i] *= sc;
+    } else {
+      std::vector<float> f(2 * n);
+      if (cudaMemcpy(f.data(), c->B.psi, n * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+      for (size_t i = 0; i < 2 * n; ++i) psi[i] = (double)f[i] * sc;
+    }
+  }
+  return MG_OK;
+}
+
+mg_status mg_get_observables(mg_ctx* c, double* norm, double* energy, double* mean_q, double* mean_p) {
+  if (!c) return MG_ERR_ARG;
+  if (!c->state_set || !c->pot_set) return MG_ERR_STATE;
+  mg_status s = read_status(c);
+  if (s != MG_OK) return s;
+  const Plan& P = c->P;
+  void* targs[] = {&c->P, &c->B};
+  s = launch_plain(c, obs_tables_kernel(), targs, 0);
+  void* fn = obs_kernel(P.prec, P.pot_kind);
+  for (int l = P.D - 1; l >= 0 && s == MG_OK; --l) {
+    int mode = 0;
+    void* args[] = {&c->P, &c->B, &l, &mode};
+    s = launch_plain(c, fn, args, P.smem_bytes);
+  }
+  if (s == MG_OK) {
+    int l = P.D - 1, mode = 1;
+    void* args[] = {&c->P, &c->B, &l, &mode};
+    s = launch_plain(c, fn, args, P.smem_bytes);
+  }
+  if (s != MG_OK) return s;
+  s = read_status(c);
+  if (s != MG_OK) return s;
+  const int nb = P.nblocks;
+  std::vector<double> part(2ull * nb * PSTRIDE);
+  if (cudaMemcpy(part.data(), c->B.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MG_ERR_CUDA;
+  double ctrl[17];
+  if (cudaMemcpy(ctrl, c->B.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+  const int D = P.D;
+  double k[PSTRIDE] = {0}, v[PSTRIDE] = {0};
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < D + 2; ++i) {
+      k[i] += part[(size_t)b * PSTRIDE + i];
+      v[i] += part[((size_t)nb + b) * PSTRIDE + i];
+    }
+  if (norm) *norm = v[0];
+  if (energy) *energy = k[D + 1] / k[0] + v[D + 1] / v[0];
+  for (int a = 0; a < D; ++a) {
+    if (mean_q) mean_q[a] = v[1 + a] / v[0];
+    if (mean_p) mean_p[a] = ctrl[8 + a] + P.dp[a] * k[1 + a] / k[0];
+  }
+  return MG_OK;
+}
+
+int64_t mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : -1; }
+
+const char* mg_status_string(int s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MG_ERR_CUDA: return "CUDA runtime error";
+    case MG_ERR_TIMEOUT: return "grid barrier timed out";
+    case MG_ERR_NONFINITE: return "non-finite norm or reduction";
+    case MG_ERR_UNSTABLE: return "grid centre diverged (time step beyond the Verlet stability limit)";
+    case MG_ERR_STATE: return "potential or state not set";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,910 @@
+// Device side of the moving-grid split-operator propagator (sm_103a).
+//
+// One persistent cooperative kernel runs a whole mg_propagate call: every
+// kinetic substep U_T,adpt (eq:T_split_substep_adaptive) and potential
+// substep U_V,adpt (Sec. II.G.1) of every step, with the grid centres (q, p)
+// updated in between from grid-wide reductions (the Ehrenfest averages of
+// eq:eom_qt_case_III_T and eq:eom_pt_solution_case_III_V).
+//
+// Work decomposition.  The state is a row-major D-dimensional array.  A
+// "pass" applies 1D transforms along one axis l: tiles of W adjacent lines are
+// staged in shared memory (coalesced global access), transformed with a
+// mixed-radix Stockham FFT (radix 2/3/4/8) in shared memory, and written
+// back.  The diagonal multipliers of the method are fused into the passes:
+//   forward pass along l:   u * A_l[j_l]                then FFT_l
+//   inverse pass along l:   phi * K_l[k_l]  then IFFT_l then * conj(A_l[j_l]) / N_l
+// where A_l[j] = (-1)^j e^{-i p_l (j - N_l/2) dq_l / hbar} is the j-dependent
+// part of e^{-i t_KJ/hbar} (eq:t_definition) and
+// K_l[k] = e^{(i/hbar)(delta_l p_l^K - tau minv_l (p_l^K)^2 / 2)} combines the
+// kinetic phase of eq:U_T_tensor with f~(q + delta, p) f(q, p), which for a
+// grid shift delta is exactly the diagonal factor e^{i delta . p^K / hbar}.
+// The last forward pass also accumulates the kinetic moments (|phi|^2 and
+// (k - N/2)|phi|^2); the last inverse pass also applies the potential phase
+// e^{-i sigma V(x^J)/hbar} (eq:U_V_tensor) and accumulates |u|^2 dV/dq.
+// Grid-wide dependencies (the reductions, and the per-axis tables that depend
+// on their result) are separated by a capped-spin grid barrier.  When the
+// whole state fits in the CTAs' shared memory, the tiles of the first and
+// last axes stay resident across those barriers.
+//
+// Every wait in this file is bounded: a barrier that does not complete
+// within the time limit records MG_ERR_TIMEOUT and the kernel returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_plan.h"
+
+namespace mgk {
+
+template <typename T> struct VT;
+template <> struct VT<double> { using v = double2; };
+template <> struct VT<float> { using v = float2; };
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return V{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { return V{a.x * s, a.y * s}; }
+// multiply by s*i with s = +1 for the inverse and -1 for the forward transform
+template <bool INV, typename V> __device__ __forceinline__ V mul_si(V a) {
+  return INV ? V{-a.y, a.x} : V{a.y, -a.x};
+}
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+template <typename V> __device__ __forceinline__ V from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+
+// ---------------------------------------------------------------------------
+// DFT codelets of radix 2, 3, 4, 8; exponent sign -1 (forward) or +1 (inverse)
+// ---------------------------------------------------------------------------
+
+template <bool INV, int R, typename V> struct Dft;
+
+template <bool INV, typename V> struct Dft<INV, 2, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    V a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+};
+
+// Irrational codelet constants are applied as hi + lo pairs: a rounded
+// constant alone makes every butterfly non-unitary by the same ~1e-16, a bias
+// that builds up linearly over thousands of transforms.
+template <typename T> struct Split;
+template <> struct Split<double> {
+  static constexpr double r2h = 0.70710678118654757, r2l = -4.833646656726457e-17;  // 1/sqrt(2)
+  static constexpr double r3h = 0.8660254037844386, r3l = 5.0175421109034514e-17;    // sqrt(3)/2
+};
+template <> struct Split<float> {
+  static constexpr float r2h = 0.70710677f, r2l = 1.21016175e-08f;
+  static constexpr float r3h = 0.86602539f, r3l = 1.55436251e-08f;
+};
+template <typename V, typename T> __device__ __forceinline__ V cscale2(V a, T hi, T lo) {
+  return V{fma(a.x, hi, a.x * lo), fma(a.y, hi, a.y * lo)};
+}
+
+template <bool INV, typename V> struct Dft<INV, 3, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    using T = decltype(v[0].x);
+    V t = cadd(v[1], v[2]);
+    V d = csub(v[1], v[2]);
+    V m = V{v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y};
+    V e = cscale2(mul_si<INV>(d), Split<T>::r3h, Split<T>::r3l);
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, e);
+    v[2] = csub(m, e);
+  }
+};
+
+template <bool INV, typename V> struct Dft<INV, 4, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    V t2 = cadd(v[1], v[3]), t3 = mul_si<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+// Radix 8 by one decimation-in-frequency split into two 4-point DFTs.
+template <bool INV, typename V> struct Dft<INV, 8, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    using T = decltype(v[0].x);
+    V a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r] = cadd(v[r], v[r + 4]);
+      b[r] = csub(v[r], v[r + 4]);
+    }
+    b[1] = cscale2(cadd(b[1], mul_si<INV>(b[1])), Split<T>::r2h, Split<T>::r2l);  // * e^{s i pi/4}
+    b[2] = mul_si<INV>(b[2]);                                                       // * e^{s i pi/2}
+    b[3] = cscale2(csub(mul_si<INV>(b[3]), b[3]), Split<T>::r2h, Split<T>::r2l);  // * e^{3 s i pi/4}
+    Dft<INV, 4, V>::run(a);
+    Dft<INV, 4, V>::run(b);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[2 * r] = a[r];
+      v[2 * r + 1] = b[r];
+    }
+  }
+};
+
+// One Stockham autosort pass of radix R over L lines of length n (in -> out).
+template <bool INV, int R, typename V>
+__device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __restrict__ out, int n,
+                                              int L, int Ns, const V* __restrict__ tw) {
+  const int nR = n / R;
+  const int total = L * nR;
+  const int ts = n / (Ns * R);
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int line = b / nR;
+    const int j = b - line * nR;
+    const V* src = in + line * n;
+    V* dst = out + line * n;
+    V v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * nR];
+    const int k = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const V w = tw[k * r * ts];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    Dft<INV, R, V>::run(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+  }
+}
+
+// Full 1D transform of L lines; returns the buffer that holds the result.
+template <bool INV, typename V>
+__device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw) {
+  int Ns = 1;
+  for (int pi = 0; pi < ax.nrad; ++pi) {
+    const int R = ax.rad[pi];
+    if (R == 8) stockham_pass<INV, 8>(in, out, ax.n, L, Ns, tw);
+    else if (R == 4) stockham_pass<INV, 4>(in, out, ax.n, L, Ns, tw);
+    else if (R == 3) stockham_pass<INV, 3>(in, out, ax.n, L, Ns, tw);
+    else stockham_pass<INV, 2>(in, out, ax.n, L, Ns, tw);
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+    Ns *= R;
+  }
+  return in;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier with a time limit
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t BARRIER_LIMIT_NS = 5000000000ull;  // 5 s
+constexpr unsigned BARRIER_MAX_SPINS = 400000000u;
+
+// All CTAs of the (cooperative) grid must call this.  Returns false after a
+// timeout; the status word then holds ST_TIMEOUT.
+__device__ bool grid_sync(const Bufs& B, int* sflag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* cnt = B.bar;
+    unsigned* gen = B.bar + 32;
+    const unsigned g0 = ld_acquire_u32(gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(cnt, 1u);
+    int ok = 1;
+    if (prev == gridDim.x - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(gen) == g0) {
+        __nanosleep(32);
+        ++spins;
+        if ((spins & 127u) == 0 && (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS)) {
+          ok = 0;
+          atomicExch(B.status, ST_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *sflag = ok;
+  }
+  __syncthreads();
+  return *sflag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout
+// ---------------------------------------------------------------------------
+
+template <typename V> struct Smem {
+  V* tw;        // maxn twiddles of the current axis
+  V* tpre;      // maxn pre-multipliers
+  V* tpost;     // maxn post-multipliers
+  double* tv;   // NVCOL * tab_total potential columns
+  double* tc;   // tab_total values k - N/2
+  double* te;   // tab_total kinetic-energy values
+  double* red;  // (THREADS/32) * PSTRIDE
+  double* fin;  // PSTRIDE finished sums
+  V* reg[2];    // data regions
+};
+
+template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* base) {
+  Smem<V> s;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off += (bytes + 15) & ~size_t(15);
+    return p;
+  };
+  s.tw = (V*)take(sizeof(V) * P.maxn);
+  s.tpre = (V*)take(sizeof(V) * P.maxn);
+  s.tpost = (V*)take(sizeof(V) * P.maxn);
+  s.tv = (double*)take(sizeof(double) * NVCOL * P.tab_total);
+  s.tc = (double*)take(sizeof(double) * P.tab_total);
+  s.te = (double*)take(sizeof(double) * P.tab_total);
+  s.red = (double*)take(sizeof(double) * (THREADS / 32) * PSTRIDE);
+  s.fin = (double*)take(sizeof(double) * PSTRIDE);
+  s.reg[0] = (V*)take(P.region_bytes);
+  s.reg[1] = (V*)take(P.region_bytes);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Potentials: V (as a phase -sigma V / hbar, folded into the tables) and grad V
+// ---------------------------------------------------------------------------
+
+// Per-point evaluation from per-axis tables.  th = -sigma V / hbar (or V
+// itself when the tables were built with scale 1), g = grad V.
+template <int KIND>
+__device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const int* idx, double sgh,
+                                       double& th, double* g) {
+  const int TT = P.tab_total;
+  const int D = P.D;
+#define COL(c, a) tv[(c) * TT + P.ax[a].toff + idx[a]]
+  if (KIND == POT_HARMONIC) {
+    if (!P.pot_general) {
+      th = 0;
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < D) {
+          th += COL(0, a);
+          g[a] = COL(1, a);
+        }
+    } else {
+      double d[MAXD];
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < D) d[a] = COL(0, a);
+      double v = 0;
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < D) {
+          double s = 0;
+#pragma unroll
+          for (int b = 0; b < MAXD; ++b)
+            if (b < D) s += P.pot[a * D + b] * d[b];
+          g[a] = s;
+          v += d[a] * s;
+        }
+      th = 0.5 * sgh * v;
+    }
+  } else if (KIND == POT_ATOM_DIATOM) {
+    const double gR = COL(0, 0), dgR = COL(1, 0), sgR = COL(2, 0);
+    const double sf = COL(0, 1), df = COL(1, 1), h = COL(2, 1), dh = COL(3, 1);
+    th = sf + sgR * h;
+    g[0] = dgR * h;
+    g[1] = df + gR * dh;
+  } else if (KIND == POT_HENON_HEILES) {
+    const double lam = P.pot[0];
+    double x[MAXD], x2[MAXD];
+    double s1 = 0, cpl = 0;
+#pragma unroll
+    for (int a = 0; a < MAXD; ++a)
+      if (a < D) {
+        x[a] = COL(0, a);
+        x2[a] = COL(2, a);
+        s1 += COL(1, a);
+        g[a] = COL(3, a);
+      }
+#pragma unroll
+    for (int a = 0; a + 1 < MAXD; ++a)
+      if (a + 1 < D) {
+        cpl += x2[a] * x[a + 1];
+        g[a] += 2.0 * lam * x[a] * x[a + 1];
+        g[a + 1] += lam * x2[a];
+      }
+    th = s1 + sgh * lam * cpl;
+  } else {  // POT_SECREST_JOHNSON
+    const double c = COL(0, 1);
+    th = COL(0, 0) + COL(2, 0) * c;
+    const double e = COL(3, 0) * c;
+    g[0] = COL(1, 0) + e;
+    g[1] = -e;
+  }
+#undef COL
+}
+
+// Potential columns of one table entry (axis a, coordinate x).
+__device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, double sgh) {
+  const int TT = P.tab_total;
+  double c[NVCOL] = {0, 0, 0, 0, 0};
+  if (P.pot_kind == POT_HARMONIC) {
+    const double d = x - P.pot[P.D * P.D + a];
+    if (!P.pot_general) {
+      const double k = P.pot[a * P.D + a];
+      c[0] = sgh * 0.5 * k * d * d;
+      c[1] = k * d;
+    } else {
+      c[0] = d;
+    }
+  } else if (P.pot_kind == POT_ATOM_DIATOM) {
+    const double Dm = P.pot[0], aa = P.pot[1], re = P.pot[2], A = P.pot[3], be = P.pot[4];
+    if (a == 0) {
+      const double g = A * exp(-be * x);
+      c[0] = g;
+      c[1] = -be * g;
+      c[2] = sgh * g;
+    } else {
+      const double em = exp(-aa * (x - re));
+      const double ep = exp(0.5 * be * x), en = exp(-0.5 * be * x);
+      c[0] = sgh * Dm * (1.0 - em) * (1.0 - em);
+      c[1] = 2.0 * Dm * (1.0 - em) * aa * em;
+      c[2] = ep + en;
+      c[3] = 0.5 * be * (ep - en);
+    }
+  } else if (P.pot_kind == POT_HENON_HEILES) {
+    const double lam = P.pot[0];
+    c[0] = x;
+    c[1] = sgh * (0.5 * x * x - (a >= 1 ? lam * x * x * x / 3.0 : 0.0));
+    c[2] = x * x;
+    c[3] = x - (a >= 1 ? lam * x * x : 0.0);
+  } else {  // SECREST_JOHNSON
+    const double Dm = P.pot[0], be = P.pot[1], al = P.pot[2];
+    if (a == 0) {
+      const double e1 = exp(-be * x), ea = exp(al * x);
+      c[0] = sgh * Dm * (1.0 - e1) * (1.0 - e1);
+      c[1] = 2.0 * Dm * (1.0 - e1) * be * e1;
+      c[2] = sgh * ea;
+      c[3] = al * ea;
+    } else {
+      c[0] = exp(-al * x);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NVCOL; ++k) __stcg(B.tabV + k * TT + e, c[k]);
+}
+
+enum { TB_K = 1, TB_V = 2, TB_A = 4, TB_E = 8 };
+
+// Distributed construction of the per-axis tables: every thread of the grid
+// builds at most a few entries.  A grid barrier must follow before use.
+__device__ void build_tables(const Plan& P, const Bufs& B, int what, double tau, const double* delta,
+                             const double* p, const double* q, double sgh) {
+  const int D = P.D;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.tab_total; e += gridDim.x * blockDim.x) {
+    int a = 0;
+    while (a + 1 < D && e >= P.ax[a + 1].toff) ++a;
+    const int j = e - P.ax[a].toff;
+    const int n = P.ax[a].n;
+    const double c = (double)(j - n / 2);
+    if (what & TB_K) {
+      const double pk = p[a] + c * P.dp[a];
+      const double th = (delta[a] * pk - 0.5 * tau * P.minv[a] * pk * pk) / P.hbar;
+      double s, co;
+      sincos(th, &s, &co);
+      __stcg(B.tabK + e, make_double2(co, s));
+    }
+    if (what & TB_A) {
+      const double th = -p[a] * c * P.dq[a] / P.hbar;
+      double s, co;
+      sincos(th, &s, &co);
+      const double sg = (j & 1) ? -1.0 : 1.0;
+      __stcg(B.tabA + e, make_double2(sg * co, sg * s));
+      // conj(A)/N by division: a rounded 1/N would bias every inverse transform
+      __stcg(B.tabAi + e, make_double2(sg * co / (double)n, -sg * s / (double)n));
+    }
+    if (what & TB_V) vcolumns(P, B, e, a, q[a] + c * P.dq[a], sgh);
+    if (what & TB_E) {
+      const double pk = p[a] + c * P.dp[a];
+      __stcg(B.tabE + e, 0.5 * P.minv[a] * pk * pk);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: deterministic per-CTA partials, then a fixed-order finish
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename V>
+__device__ void block_partials(const Bufs& B, const Smem<V>& S, int slot, const double* acc, int nv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < MAXD + 2; ++v)
+    if (v < nv) {
+      const double x = warp_sum(acc[v]);
+      if (lane == 0) S.red[warp * PSTRIDE + v] = x;
+    }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += S.red[w * PSTRIDE + threadIdx.x];
+    __stcg(B.part + ((size_t)slot * gridDim.x + blockIdx.x) * PSTRIDE + threadIdx.x, s);
+  }
+  __syncthreads();
+}
+
+// Sum the per-CTA partials of `slot` in a fixed order; result in S.fin.
+template <typename V> __device__ void finish(const Bufs& B, const Smem<V>& S, int slot, int nv) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int v = 0; v < nv; ++v) {
+      double s = 0;
+      for (int b = lane; b < (int)gridDim.x; b += 32)
+        s += __ldcg(B.part + ((size_t)slot * gridDim.x + b) * PSTRIDE + v);
+      s = warp_sum(s);
+      if (lane == 0) S.fin[v] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// One pass along one axis
+// ---------------------------------------------------------------------------
+
+enum { PRE_NONE = 0, PRE_A = 1, PRE_K = 2 };
+enum { RED_NONE = 0, RED_KIN = 1, RED_V = 2, RED_OBS_KIN = 3, RED_OBS_V = 4 };
+
+struct PassArgs {
+  int l;
+  int from_smem;  // input already in smem region `res_in` (single chunk)
+  int keep;       // leave the result in smem (single chunk), no global store
+  int fft;        // apply the 1D transform
+  int pre, post;  // multipliers (post: conj(A)/N)
+  int red;        // fused reduction / potential phase
+  int slot;       // partial-sum slot
+  double sgh;     // -sigma/hbar (general harmonic only; else folded in tables)
+  const void* src;
+  void* dst;
+  const double* q;  // grid centre (RED_OBS_V)
+};
+
+// Multi-index of element j of line (o, i) of axis l.
+__device__ __forceinline__ void decode(const Plan& P, int l, unsigned o, unsigned i, int j, int* idx) {
+  for (int a = l - 1; a >= 0; --a) {
+    const unsigned n = (unsigned)P.N[a];
+    idx[a] = (int)(o % n);
+    o /= n;
+  }
+  for (int a = P.D - 1; a > l; --a) {
+    const unsigned n = (unsigned)P.N[a];
+    idx[a] = (int)(i % n);
+    i /= n;
+  }
+  idx[l] = j;
+}
+
+template <typename T, bool INV, int KIND>
+__device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const Smem<typename VT<T>::v>& S,
+                         int res_in) {
+  using V = typename VT<T>::v;
+  const AxisPlan& ax = P.ax[A.l];
+  const int n = ax.n, W = ax.W, D = P.D;
+  const bool contig = (A.l == D - 1);
+  const int64_t s = ax.stride;
+  const int64_t tpo = contig ? 1 : s / W;  // tiles per outer index
+  const int64_t ws = contig ? n : 1;       // element step between lines of a tile
+  const int64_t es = contig ? 1 : s;       // element step along the axis
+
+  // tables of this pass
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (A.fft) S.tw[j] = from_d2<V>(__ldcg(B.tw + ax.toff + j));
+    if (A.pre) S.tpre[j] = from_d2<V>(__ldcg((A.pre == PRE_A ? B.tabA : B.tabK) + ax.toff + j));
+    if (A.post) S.tpost[j] = from_d2<V>(__ldcg(B.tabAi + ax.toff + j));
+  }
+  if (A.red != RED_NONE) {
+    for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
+      S.tc[e] = __ldcg(B.tabC + e);
+      if (A.red == RED_OBS_KIN) S.te[e] = __ldcg(B.tabE + e);
+      if (A.red == RED_V || A.red == RED_OBS_V)
+        for (int c = 0; c < NVCOL; ++c) S.tv[c * P.tab_total + e] = __ldcg(B.tabV + c * P.tab_total + e);
+    }
+  }
+  __syncthreads();
+
+  double acc[MAXD + 2];
+#pragma unroll
+  for (int v = 0; v < MAXD + 2; ++v) acc[v] = 0;
+
+  const int64_t bid = blockIdx.x, nb = gridDim.x;
+  const int64_t mine = bid < ax.ntiles ? (ax.ntiles - bid + nb - 1) / nb : 0;
+  const V* src = (const V*)A.src;
+  V* dst = (V*)A.dst;
+  int res = -1;
+  const int chunk = A.from_smem || A.keep ? (int)mine : ax.tpc;
+  for (int64_t c0 = 0; c0 < mine; c0 += chunk) {
+    const int nt = (int)(mine - c0 < chunk ? mine - c0 : chunk);
+    const int cnt = nt * W * n;
+    V* cur;
+    if (A.from_smem) {
+      cur = S.reg[res_in];
+      if (A.pre)
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+          const int j = e % n;
+          cur[e] = cmul(cur[e], S.tpre[j]);
+        }
+    } else {
+      cur = S.reg[0];
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int ti = e / (W * n);
+        const int rem = e - ti * W * n;
+        int w, j;
+        if (contig) { w = rem / n; j = rem - w * n; }
+        else { j = rem / W; w = rem - j * W; }
+        const int64_t t = bid + (c0 + ti) * nb;
+        const int64_t o = t / tpo;
+        const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
+        V v = __ldcg(src + base + j * es + w * ws);
+        if (A.pre) v = cmul(v, S.tpre[j]);
+        cur[(ti * W + w) * n + j] = v;
+      }
+    }
+    __syncthreads();
+    if (A.fft) cur = stockham<INV>(cur, cur == S.reg[0] ? S.reg[1] : S.reg[0], nt * W, ax, S.tw);
+
+    // epilogue
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int ti = e / (W * n);
+      const int rem = e - ti * W * n;
+      int w, j;
+      if (contig) { w = rem / n; j = rem - w * n; }
+      else { j = rem / W; w = rem - j * W; }
+      const int64_t t = bid + (c0 + ti) * nb;
+      const int64_t o = t / tpo;
+      const int si = (ti * W + w) * n + j;
+      V v = cur[si];
+      if (A.post) v = cmul(v, S.tpost[j]);
+      if (A.red != RED_NONE) {
+        int idx[MAXD];
+        const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
+        const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
+        decode(P, A.l, lo, li, j, idx);
+        const double2 d = to_d2(v);
+        const double w2 = d.x * d.x + d.y * d.y;
+        acc[0] += w2;
+        if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
+          double te = 0;
+#pragma unroll
+          for (int a = 0; a < MAXD; ++a)
+            if (a < D) {
+              acc[1 + a] += S.tc[P.ax[a].toff + idx[a]] * w2;
+              if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
+            }
+          if (A.red == RED_OBS_KIN) acc[D + 1] += te * w2;
+        } else {
+          double th, g[MAXD];
+          vpoint<KIND>(P, S.tv, idx, A.sgh, th, g);
+          if (A.red == RED_V) {
+#pragma unroll
+            for (int a = 0; a < MAXD; ++a)
+              if (a < D) acc[1 + a] += g[a] * w2;
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            v = from_d2<V>(make_double2(d.x * cs - d.y * sn, d.x * sn + d.y * cs));
+          } else {  // observables: <x> and <V>
+#pragma unroll
+            for (int a = 0; a < MAXD; ++a)
+              if (a < D) acc[1 + a] += (A.q[a] + S.tc[P.ax[a].toff + idx[a]] * P.dq[a]) * w2;
+            acc[D + 1] += th * w2;
+          }
+        }
+      }
+      if (A.keep) cur[si] = v;
+      else if (dst) {
+        const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
+        __stcg(dst + base + j * es + w * ws, v);
+      }
+    }
+    __syncthreads();
+    res = cur == S.reg[0] ? 0 : 1;
+  }
+  if (A.red != RED_NONE) {
+    const int nv = (A.red == RED_OBS_KIN || A.red == RED_OBS_V) ? D + 2 : D + 1;
+    block_partials(B, S, A.slot, acc, nv);
+  }
+  return res;
+}
+
+// Store tiles of axis D-1 that are resident in smem region `res` to psi.
+template <typename T> __device__ void flush_resident(const Plan& P, const Bufs& B,
+                                                      const Smem<typename VT<T>::v>& S, int res) {
+  using V = typename VT<T>::v;
+  const AxisPlan& ax = P.ax[P.D - 1];
+  const int n = ax.n, W = ax.W;
+  const int64_t bid = blockIdx.x, nb = gridDim.x;
+  const int64_t mine = bid < ax.ntiles ? (ax.ntiles - bid + nb - 1) / nb : 0;
+  V* dst = (V*)B.psi;
+  const int cnt = (int)mine * W * n;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int ti = e / (W * n);
+    const int rem = e - ti * W * n;
+    const int64_t t = bid + (int64_t)ti * nb;
+    __stcg(dst + t * W * n + rem, S.reg[res][e]);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The persistent propagation kernel
+// ---------------------------------------------------------------------------
+
+// Substep sizes of kinetic unit u (a kinetic substep, optionally followed by a
+// fused potential substep), with the half-steps of neighbouring symmetric
+// stages merged (U_T(a) U_T(b) = U_T(a+b) also for the moving grid, because
+// <p> is invariant under the kinetic substep).
+__device__ __forceinline__ void unit_coeffs(const Run& R, const double* gam, int64_t u, double& tau,
+                                            double& sig, bool& hasv) {
+  const int S = R.S;
+  const int64_t nS = R.n_steps * S;
+  const double dt = R.dt;
+  const int k = (int)(u % S);
+  if (R.split == SPLIT_TVT) {
+    if (u == 0) tau = 0.5 * gam[0] * dt;
+    else if (u == nS) tau = 0.5 * gam[S - 1] * dt;
+    else tau = 0.5 * (gam[(k + S - 1) % S] + gam[k]) * dt;
+    hasv = u < nS;
+    sig = gam[k] * dt;
+  } else if (R.split == SPLIT_VTV) {
+    tau = gam[k] * dt;
+    hasv = true;
+    sig = (u == nS - 1) ? 0.5 * gam[S - 1] * dt : 0.5 * (gam[k] + gam[(k + 1) % S]) * dt;
+  } else {  // first-order TV: V(g_k dt) T(g_k dt) per stage
+    tau = gam[k] * dt;
+    hasv = u < nS - 1;
+    sig = gam[(k + 1) % S] * dt;
+  }
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_propagate(const __grid_constant__ Plan P, const __grid_constant__ Bufs B, const __grid_constant__ Run RN) {
+  using V = typename VT<T>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sflag;
+  const Smem<V> S = carve<V>(P, smem_raw);
+  const int D = P.D;
+  // an unreported error from an earlier launch makes every later launch a no-op
+  if (__ldcg(B.status) != ST_OK) return;
+  double q[MAXD], p[MAXD], qn[MAXD], delta[MAXD];
+#pragma unroll
+  for (int a = 0; a < MAXD; ++a) {
+    q[a] = a < D ? __ldcg(B.ctrl + a) : 0.0;
+    p[a] = a < D ? __ldcg(B.ctrl + 8 + a) : 0.0;
+    qn[a] = q[a];
+    delta[a] = 0.0;
+  }
+  const double* gam = B.gamma;
+  int res = -1;
+  bool kept = false;
+  int err = ST_OK;
+
+  if (RN.lead_v) {
+    const double sig = (RN.split == SPLIT_VTV ? 0.5 : 1.0) * gam[0] * RN.dt;
+    const double sgh = -sig / P.hbar;
+    build_tables(P, B, TB_V, 0.0, delta, p, q, sgh);
+    if (!grid_sync(B, &sflag)) return;
+    PassArgs a{};
+    a.l = D - 1; a.fft = 0; a.red = RED_V; a.slot = 1; a.sgh = sgh;
+    a.keep = P.resident; a.src = B.psi; a.dst = B.psi;
+    res = axis_pass<T, false, KIND>(P, B, a, S, -1);
+    kept = P.resident;
+    if (!grid_sync(B, &sflag)) return;
+    finish(B, S, 1, D + 1);
+    const double n = S.fin[0];
+    if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
+    for (int b = 0; b < D; ++b) {
+      const double g = S.fin[1 + b] / n;
+      if (!isfinite(g)) { err = ST_NONFINITE; goto done; }
+      if (RN.motion != GRID_FIXED) {
+        const double dpn = sig * g;
+        if (fabs(dpn) > 10.0 * P.N[b] * P.dp[b]) { err = ST_UNSTABLE; goto done; }
+        p[b] -= dpn;
+      }
+    }
+    build_tables(P, B, TB_A, 0.0, delta, p, q, 0.0);
+    if (!grid_sync(B, &sflag)) return;
+  }
+
+  for (int64_t u = 0; u < RN.n_units; ++u) {
+    double tau, sig;
+    bool hasv;
+    unit_coeffs(RN, gam, u, tau, sig, hasv);
+    // forward transform, kinetic moments on the last pass
+    for (int i = 0; i < D; ++i) {
+      const bool last = (i == D - 1);
+      PassArgs a{};
+      a.l = D - 1 - i; a.fft = 1; a.pre = PRE_A;
+      a.from_smem = (i == 0 && kept);
+      a.keep = last && P.resident;
+      a.red = last ? RED_KIN : RED_NONE; a.slot = 0;
+      a.src = B.psi; a.dst = B.psi;
+      res = axis_pass<T, false, KIND>(P, B, a, S, res);
+      kept = a.keep;
+      if (!last && !grid_sync(B, &sflag)) return;
+    }
+    if (!grid_sync(B, &sflag)) return;
+    finish(B, S, 0, D + 1);
+    {
+      const double n = S.fin[0];
+      if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
+      for (int b = 0; b < D; ++b) {
+        const double pi = p[b] + P.dp[b] * (S.fin[1 + b] / n);
+        if (!isfinite(pi)) { err = ST_NONFINITE; goto done; }
+        const double mom = RN.motion == GRID_ADAPTIVE ? pi : p[b];
+        delta[b] = RN.motion == GRID_FIXED ? 0.0 : tau * P.minv[b] * mom;
+        if (fabs(delta[b]) > 10.0 * P.N[b] * P.dq[b]) { err = ST_UNSTABLE; goto done; }
+        qn[b] = q[b] + delta[b];
+      }
+    }
+    build_tables(P, B, TB_K | (hasv ? TB_V : 0), tau, delta, p, qn, -sig / P.hbar);
+    if (!grid_sync(B, &sflag)) return;
+#pragma unroll
+    for (int b = 0; b < MAXD; ++b) q[b] = qn[b];
+    // inverse transform, potential substep fused into the last pass
+    for (int i = 0; i < D; ++i) {
+      const bool last = (i == D - 1);
+      PassArgs a{};
+      a.l = i; a.fft = 1; a.pre = PRE_K; a.post = 1;
+      a.from_smem = (i == 0 && kept);
+      a.keep = last && hasv && P.resident;
+      a.red = (last && hasv) ? RED_V : RED_NONE; a.slot = 1; a.sgh = -sig / P.hbar;
+      a.src = B.psi; a.dst = B.psi;
+      res = axis_pass<T, true, KIND>(P, B, a, S, res);
+      kept = a.keep;
+      if (!last && !grid_sync(B, &sflag)) return;
+    }
+    if (hasv) {
+      if (!grid_sync(B, &sflag)) return;
+      finish(B, S, 1, D + 1);
+      const double n = S.fin[0];
+      if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
+      for (int b = 0; b < D; ++b) {
+        const double g = S.fin[1 + b] / n;
+        if (!isfinite(g)) { err = ST_NONFINITE; goto done; }
+        if (RN.motion != GRID_FIXED) {
+          const double dpn = sig * g;
+          if (fabs(dpn) > 10.0 * P.N[b] * P.dp[b]) { err = ST_UNSTABLE; goto done; }
+          p[b] -= dpn;
+        }
+      }
+      build_tables(P, B, TB_A, 0.0, delta, p, q, 0.0);
+      if (!grid_sync(B, &sflag)) return;
+    }
+  }
+  if (kept) flush_resident<T>(P, B, S, res);
+done:
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int a = 0; a < D; ++a) {
+      B.ctrl[a] = q[a];
+      B.ctrl[8 + a] = p[a];
+    }
+    if (err != ST_OK) atomicExch(B.status, err);
+  }
+}
+
+// Tables A/Ainv for the current p-centre (after a state upload).
+__global__ void __launch_bounds__(THREADS) k_init_tables(const __grid_constant__ Plan P,
+                                                          const __grid_constant__ Bufs B) {
+  double p[MAXD], q[MAXD], z[MAXD];
+  for (int a = 0; a < MAXD; ++a) {
+    p[a] = a < P.D ? B.ctrl[8 + a] : 0.0;
+    q[a] = a < P.D ? B.ctrl[a] : 0.0;
+    z[a] = 0.0;
+  }
+  build_tables(P, B, TB_A, 0.0, z, p, q, 0.0);
+}
+
+// Observables: tables of V (unscaled) and of the kinetic energy.
+__global__ void __launch_bounds__(THREADS) k_obs_tables(const __grid_constant__ Plan P,
+                                                         const __grid_constant__ Bufs B) {
+  double p[MAXD], q[MAXD], z[MAXD];
+  for (int a = 0; a < MAXD; ++a) {
+    p[a] = a < P.D ? B.ctrl[8 + a] : 0.0;
+    q[a] = a < P.D ? B.ctrl[a] : 0.0;
+    z[a] = 0.0;
+  }
+  build_tables(P, B, TB_V | TB_E, 0.0, z, p, q, 1.0);
+}
+
+// Observables: one forward pass (out of place into scratch) or the V pass.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(THREADS)
+    k_obs_pass(const __grid_constant__ Plan P, const __grid_constant__ Bufs B, int l, int mode) {
+  using V = typename VT<T>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<V> S = carve<V>(P, smem_raw);
+  double q[MAXD];
+  for (int a = 0; a < MAXD; ++a) q[a] = a < P.D ? B.ctrl[a] : 0.0;
+  PassArgs a{};
+  a.l = l;
+  a.q = q;
+  a.sgh = 1.0;
+  if (mode == 0) {  // forward transform pass; kinetic moments on axis 0
+    a.fft = 1; a.pre = PRE_A;
+    a.red = (l == 0) ? RED_OBS_KIN : RED_NONE; a.slot = 0;
+    a.src = (l == P.D - 1) ? B.psi : (const void*)B.scratch;
+    a.dst = B.scratch;
+  } else {  // <V>, <x>, norm over psi (read only)
+    a.red = RED_OBS_V; a.slot = 1;
+    a.src = B.psi; a.dst = nullptr;
+  }
+  axis_pass<T, false, KIND>(P, B, a, S, -1);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (C++ linkage, used by mg_capi.cu)
+// ---------------------------------------------------------------------------
+
+template <typename T, int KIND> static void* prop_fn() { return (void*)k_propagate<T, KIND>; }
+template <typename T, int KIND> static void* obs_fn() { return (void*)k_obs_pass<T, KIND>; }
+
+void* propagate_kernel(int prec, int kind) {
+  if (prec != 0) return nullptr;
+  switch (kind) {
+    case POT_HARMONIC: return prop_fn<double, POT_HARMONIC>();
+    case POT_ATOM_DIATOM: return prop_fn<double, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES: return prop_fn<double, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON: return prop_fn<double, POT_SECREST_JOHNSON>();
+  }
+  return nullptr;
+}
+
+void* obs_kernel(int prec, int kind) {
+  if (prec != 0) return nullptr;
+  switch (kind) {
+    case POT_HARMONIC: return obs_fn<double, POT_HARMONIC>();
+    case POT_ATOM_DIATOM: return obs_fn<double, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES: return obs_fn<double, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON: return obs_fn<double, POT_SECREST_JOHNSON>();
+  }
+  return nullptr;
+}
+
+void* init_tables_kernel() { return (void*)k_init_tables; }
+void* obs_tables_kernel() { return (void*)k_obs_tables; }
+
+}  // namespace mgk

@@ -1,0 +1,79 @@
+// Plain-old-data descriptors shared by the host planner (mg_capi.cu) and the
+// device kernels (mg_kernels.cu).  No CUDA types beyond double2.
+#pragma once
+#include <stdint.h>
+#include <vector_types.h>
+
+namespace mgk {
+
+constexpr int MAXD = 8;        // axes
+constexpr int MAXRAD = 12;     // Stockham passes per axis
+constexpr int MAXN = 1024;     // longest axis
+constexpr int PSTRIDE = 16;    // doubles per CTA partial-sum record
+constexpr int NVCOL = 5;       // potential-table columns per axis
+constexpr int MAX_STAGES = 625;
+constexpr int THREADS = 256;   // threads per CTA of every kernel
+
+enum { POT_HARMONIC = 0, POT_ATOM_DIATOM = 1, POT_HENON_HEILES = 2, POT_SECREST_JOHNSON = 3 };
+enum { SPLIT_TVT = 0, SPLIT_VTV = 1, SPLIT_TV = 2 };
+enum { GRID_ADAPTIVE = 0, GRID_CENTRE_P = 1, GRID_FIXED = 2 };
+enum { ST_OK = 0, ST_TIMEOUT = -4, ST_NONFINITE = -5, ST_UNSTABLE = -6 };
+
+// One axis of the tensor-product grid and how its 1D transforms are tiled.
+struct AxisPlan {
+  int n;                 // points on the axis (N_l)
+  int nrad;              // Stockham passes
+  int rad[MAXRAD];       // radix of each pass (2, 3, 4 or 8)
+  int W;                 // lines per tile (adjacent in the contiguous index)
+  int tpc;               // tiles a CTA processes per smem chunk
+  int toff;              // offset of this axis in the per-axis tables
+  int64_t stride;        // element stride of the axis (prod of N_m, m > l)
+  int64_t outer;         // prod of N_m, m < l
+  int64_t ntiles;        // tiles in one pass over the whole grid
+};
+
+struct Plan {
+  int D;
+  int prec;              // 0 = FP64, 1 = FP32 storage
+  int nblocks;           // CTAs of the persistent kernel (all co-resident)
+  int resident;          // tiles of axes 0 and D-1 stay in smem across barriers
+  int maxn;              // longest axis
+  int tab_total;         // sum of N_l
+  int region_bytes;      // bytes of each of the two smem data regions
+  int smem_bytes;        // dynamic smem per CTA
+  int64_t npts;
+  int64_t N[MAXD];
+  double dq[MAXD], dp[MAXD], minv[MAXD], hbar;
+  AxisPlan ax[MAXD];
+  int pot_kind;
+  int pot_general;       // harmonic potential with a non-diagonal K
+  double pot[MAXD * MAXD + MAXD];
+};
+
+// Device buffers, all inside the caller's workspace except psi.
+struct Bufs {
+  void* psi;             // scaled state u (complex128 or complex64)
+  double* ctrl;          // [0,8) q, [8,16) p, [16] t
+  unsigned* bar;         // [0] arrival count, [32] generation
+  int* status;
+  double* part;          // [2][nblocks][PSTRIDE] per-CTA partial sums
+  double2* tw;           // forward twiddles e^{-2 pi i m / N_l}, per axis
+  double2* tabA;         // A_l[j] = (-1)^j e^{-i p_l (j - N_l/2) dq_l / hbar}
+  double2* tabAi;        // conj(A_l[j]) / N_l
+  double2* tabK;         // kinetic multiplier per axis (Sec. II.G.2, with the grid shift)
+  double* tabV;          // [NVCOL][tab_total] potential columns
+  double* tabC;          // k - N_l/2 as double
+  double* tabE;          // per-axis kinetic energy minv_l (p_l^K)^2 / 2
+  const double* gamma;   // composition coefficients
+  double2* scratch;      // npts complex128 (observables, host staging)
+};
+
+// One persistent launch.
+struct Run {
+  int64_t n_units;       // kinetic units (each optionally followed by a fused V)
+  int64_t n_steps;
+  int split, motion, S, lead_v;
+  double dt;
+};
+
+}  // namespace mgk

@@ -1,0 +1,73 @@
+"""The C-ABI library loads on a host without a GPU and exports every entry
+point that include/mgrid.h declares; host-only calls behave as documented."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_06412_gb300 import _build, capi
+
+    if not os.path.exists(capi.LIB_PATH):
+        _build.build()
+    return capi.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_workspace_size_and_rejections(lib):
+    from paper_1909_06412_gb300 import capi
+
+    assert capi.mg_workspace_bytes((256, 256)) >= 256 * 256 * 16
+    assert capi.mg_workspace_bytes((10, 7)) == 0      # odd length
+    assert capi.mg_workspace_bytes((10, 12)) == 0     # factor 5
+    assert capi.mg_workspace_bytes((2048,)) == 0      # longer than supported
+    assert capi.mg_workspace_bytes((12,) * 8) > 12 ** 8 * 16
+    assert capi.mg_workspace_bytes((8, 8), precision=7) == 0
+
+
+def test_status_strings_and_host_helpers(lib):
+    from paper_1909_06412_gb300 import capi
+
+    for code in range(0, -8, -1):
+        assert lib.mg_status_string(code)
+    # <r> of the Morse ground state (digamma closed form) vs the oracle's quadrature
+    import oracle
+
+    m = 0.5 * 1822.888486
+    assert abs(capi.mg_morse_mean(0.17, 1.0, 1.4, m) - oracle.morse_mean(0.17, 1.0, 1.4, m)) < 1e-10
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    import ctypes
+
+    h = ctypes.c_void_p()
+    N = np.array([8, 8], dtype=np.int64)
+    dq = np.array([0.5, 0.5])
+    minv = np.eye(2).ravel()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(minv), 1.0, 0, None, None, 0, None) == -1
+    bad = np.array([[1.0, 0.2], [0.2, 1.0]]).ravel()
+    fake = ctypes.c_void_p(256)
+    assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(bad), 1.0, 0, fake, fake, 1 << 30, None) == -2
+    assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(minv), -1.0, 0, fake, fake, 1 << 30, None) == -1
