@@ -132,6 +132,34 @@ double mg_morse_mean(double Dm, double a, double re, double mass, double hbar);
 
 const char* mg_status_string(int status);
 
+/* Propagation without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory -
+ * code running inside a host application or framework that owns all device
+ * memory through its own pool and forbids plug-ins to call cudaMalloc, or a
+ * latency-critical loop in which an allocation (which may synchronise the
+ * device) is not acceptable.  It does what mg_create + mg_set_potential +
+ * mg_set_state(NULL, q, p, 0) + mg_propagate + mg_get_state(NULL, q, p, ...)
+ * do, but its scratch lives in a 768 KiB array inside the library (held by
+ * every GPU that loads the library until the process exits) instead of a
+ * caller-provided workspace; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *  - d_psi: device buffer of prod(N) complex128 values holding the scaled
+ *    state u^J = psi(x^J) sqrt(prod dq_l), updated in place.  FP64 only.
+ *  - q, p: host arrays of D doubles, the grid centres on entry and on exit.
+ *  - Other arguments as in mg_create, mg_set_potential and mg_propagate.
+ *  - Limits: sum of the axis lengths <= 4096 and at most 1024 CTAs; larger
+ *    grids return MG_ERR_UNSUPPORTED before any device work.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and corrupt each other.  The call
+ *    synchronises `cuda_stream` before it returns. */
+mg_status mg_propagate_noalloc(int D, const int64_t* N, const double* dq, const double* minv, double hbar,
+                               int pot_kind, const double* pot_params, int npot, void* d_psi, double* q,
+                               double* p, int64_t n_steps, double dt, const char* scheme, int split,
+                               int grid_motion, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED = 0, 1, 2
 MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON = 0, 1, 2, 3
 
 __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "MgError", "lib", "mg_workspace_bytes",
-                                                        "mg_morse_mean"]
+                                                        "mg_morse_mean", "mg_propagate_noalloc"]
 
 _lib = None
 
@@ -185,3 +185,32 @@ class Propagator:
     @property
     def launches(self):
         return int(lib().mg_kernel_launches(self._h))
+
+
+def mg_propagate_noalloc(N, dq, minv, hbar, pot_kind, pot_params, d_psi, q, p, n_steps, dt, scheme="strang",
+                         split=MG_TVT, grid_motion=MG_GRID_ADAPTIVE, stream=None):
+    """Propagate without any device allocation by the library (for callers that
+    cannot allocate device memory).  d_psi: CUDA float64 tensor of 2*prod(N)
+    values holding the scaled state, updated in place; q, p: float64 numpy
+    arrays of the grid centres, updated in place.  Synchronises the stream."""
+    L = lib()
+    fn = L.mg_propagate_noalloc
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    fn.argtypes = [i32, vp, vp, vp, d, i32, vp, i32, vp, vp, vp, i64, d, ctypes.c_char_p, i32, i32, vp]
+    fn.restype = i32
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    D = n.size
+    dqa = _f64(dq, D)
+    mi = np.asarray(minv, dtype=np.float64)
+    mi = _f64(np.diag(mi) if mi.ndim == 1 else mi, D * D)
+    pp = _f64(pot_params)
+    for a in (q, p):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == D):
+            raise ValueError("q and p must be contiguous float64 arrays of D values (updated in place)")
+    if d_psi.dtype != __import__("torch").float64 or d_psi.numel() != 2 * int(np.prod(n)) or not d_psi.is_cuda:
+        raise ValueError("d_psi must be a CUDA float64 tensor of 2*prod(N) values")
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    rc = fn(D, _ptr(n), _ptr(dqa), _ptr(mi), float(hbar), pot_kind, _ptr(pp), pp.size,
+            ctypes.c_void_p(d_psi.data_ptr()), _ptr(q), _ptr(p), int(n_steps), float(dt), scheme.encode(),
+            split, grid_motion, s)
+    _check(rc, "mg_propagate_noalloc")

@@ -648,3 +648,260 @@ const char* mg_status_string(int s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mg_propagate_noalloc: the propagation kernel for callers that cannot
+// allocate device memory.  Its scratch (per-axis tables, per-CTA partial
+// sums, barrier words, composition coefficients, grid centres) lives in one
+// file-scope __device__ array instead of a caller-provided workspace.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 768 * 1024;  // held by every GPU that loads the library
+constexpr int NOALLOC_MAXTAB = 4096;                  // largest sum of the axis lengths
+constexpr int NOALLOC_MAXBLOCKS = 1024;               // largest persistent grid
+constexpr int NOALLOC_MAXDEV = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Offsets inside g_noalloc_scratch (fixed, independent of the grid).
+constexpr size_t NA_CTRL = 0;
+constexpr size_t NA_BAR = 256;
+constexpr size_t NA_STATUS = 512;
+constexpr size_t NA_PART = 768;
+constexpr size_t NA_TW = NA_PART + 2ull * NOALLOC_MAXBLOCKS * PSTRIDE * sizeof(double);
+constexpr size_t NA_TABA = NA_TW + NOALLOC_MAXTAB * sizeof(double2);
+constexpr size_t NA_TABAI = NA_TABA + NOALLOC_MAXTAB * sizeof(double2);
+constexpr size_t NA_TABK = NA_TABAI + NOALLOC_MAXTAB * sizeof(double2);
+constexpr size_t NA_TABV = NA_TABK + NOALLOC_MAXTAB * sizeof(double2);
+constexpr size_t NA_TABC = NA_TABV + (size_t)NVCOL * NOALLOC_MAXTAB * sizeof(double);
+constexpr size_t NA_TABE = NA_TABC + NOALLOC_MAXTAB * sizeof(double);
+constexpr size_t NA_GAMMA = NA_TABE + NOALLOC_MAXTAB * sizeof(double);
+constexpr size_t NA_END = NA_GAMMA + MAX_STAGES * sizeof(double);
+static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "static scratch too small for its layout");
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAXDEV];
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+mg_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAXDEV) return MG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MG_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MG_OK;
+}
+
+// Composition coefficients into a fixed array (no heap use).
+int scheme_fixed(const char* name, double* g, int cap) {
+  if (!name) return -1;
+  int family = -1, order = 0;
+  if (std::strcmp(name, "strang") == 0) { family = 0; order = 2; }
+  else if (std::strncmp(name, "yoshida", 7) == 0) { family = 1; order = std::atoi(name + 7); }
+  else if (std::strncmp(name, "suzuki", 6) == 0) { family = 2; order = std::atoi(name + 6); }
+  if (family < 0 || order < 2 || order > 10 || order % 2) return -1;
+  double tmp[MAX_STAGES];
+  int s = 1;
+  g[0] = 1.0;
+  for (int k = 1; 2 * k < order; ++k) {
+    const double e = 1.0 / (2 * k + 1);
+    double w[5];
+    int nw;
+    if (family == 1) {
+      const double a = 1.0 / (2.0 - std::pow(2.0, e));
+      w[0] = a; w[1] = 1.0 - 2.0 * a; w[2] = a; nw = 3;
+    } else {
+      const double a = 1.0 / (4.0 - std::pow(4.0, e));
+      w[0] = a; w[1] = a; w[2] = 1.0 - 4.0 * a; w[3] = a; w[4] = a; nw = 5;
+    }
+    if (s * nw > cap) return -1;
+    for (int b = 0; b < nw; ++b)
+      for (int i = 0; i < s; ++i) tmp[b * s + i] = w[b] * g[i];
+    s *= nw;
+    std::memcpy(g, tmp, sizeof(double) * s);
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double* dq, const double* minv,
+                                          double hbar, int pot_kind, const double* pot_params, int npot,
+                                          void* d_psi, double* q, double* p, int64_t n_steps, double dt,
+                                          const char* scheme, int split, int grid_motion, void* cuda_stream) {
+  // ---- arguments (nothing touches the device before they pass) ----
+  if (!N || !dq || !minv || !d_psi || !q || !p || (!pot_params && npot > 0)) return MG_ERR_ARG;
+  if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar) || n_steps < 0 || !std::isfinite(dt))
+    return MG_ERR_ARG;
+  if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
+    return MG_ERR_ARG;
+  if ((uintptr_t)d_psi & 15) return MG_ERR_ARG;
+  int tab_total = 0;
+  for (int l = 0; l < D; ++l) {
+    if (N[l] < 2 || N[l] % 2 || !(dq[l] > 0) || !std::isfinite(dq[l])) return MG_ERR_ARG;
+    if (!axis_supported(N[l])) return MG_ERR_UNSUPPORTED;
+    tab_total += (int)N[l];
+    if (!std::isfinite(q[l]) || !std::isfinite(p[l])) return MG_ERR_ARG;
+  }
+  if (tab_total > NOALLOC_MAXTAB) return MG_ERR_UNSUPPORTED;  // beyond the static scratch
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      const double v = minv[a * D + b];
+      if (!std::isfinite(v)) return MG_ERR_ARG;
+      if (a != b && v != 0.0) return MG_ERR_UNSUPPORTED;
+      if (a == b && !(v > 0)) return MG_ERR_ARG;
+    }
+  int need;
+  switch (pot_kind) {
+    case MG_POT_HARMONIC: need = D * D + D; break;
+    case MG_POT_ATOM_DIATOM: need = 5; if (D != 2) return MG_ERR_ARG; break;
+    case MG_POT_HENON_HEILES: need = 1; break;
+    case MG_POT_SECREST_JOHNSON: need = 3; if (D != 2) return MG_ERR_ARG; break;
+    default: return MG_ERR_ARG;
+  }
+  if (npot != need) return MG_ERR_ARG;
+  for (int i = 0; i < npot; ++i)
+    if (!std::isfinite(pot_params[i])) return MG_ERR_ARG;
+  double gam[MAX_STAGES];
+  const int S = scheme_fixed(scheme, gam, MAX_STAGES);
+  if (S <= 0) return MG_ERR_ARG;
+  if (n_steps == 0) return MG_OK;
+
+  // ---- plan (same tiling rules as a context) ----
+  Plan P;
+  std::memset(&P, 0, sizeof(Plan));
+  P.D = D;
+  P.prec = MG_FP64;
+  P.hbar = hbar;
+  P.npts = 1;
+  for (int l = 0; l < D; ++l) P.npts *= N[l];
+  for (int l = D - 1; l >= 0; --l) {
+    P.ax[l].n = (int)N[l];
+    P.ax[l].stride = (l == D - 1) ? 1 : P.ax[l + 1].stride * N[l + 1];
+  }
+  for (int l = 0; l < D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    P.N[l] = N[l];
+    P.dq[l] = dq[l];
+    P.dp[l] = 2.0 * M_PI * hbar / ((double)N[l] * dq[l]);
+    P.minv[l] = minv[l * D + l];
+    ax.outer = P.npts / (ax.n * ax.stride);
+    ax.toff = P.tab_total;
+    P.tab_total += ax.n;
+    P.maxn = std::max(P.maxn, ax.n);
+    radix_plan(ax.n, ax);
+  }
+  P.pot_kind = pot_kind;
+  std::memcpy(P.pot, pot_params, sizeof(double) * npot);
+  if (pot_kind == MG_POT_HARMONIC)
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        if (pot_params[a * D + b] != pot_params[b * D + a]) return MG_ERR_ARG;
+        if (a != b && pot_params[a * D + b] != 0.0) P.pot_general = 1;
+      }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MG_ERR_CUDA;
+  P.nblocks = std::min(NOALLOC_MAXBLOCKS, sms);
+  tile_plan(P);
+  void* fn = propagate_kernel(P.prec, pot_kind);
+  if (!fn) return MG_ERR_UNSUPPORTED;
+  if (P.smem_bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes) != cudaSuccess)
+    return MG_ERR_CUDA;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, THREADS, P.smem_bytes) != cudaSuccess || occ < 1)
+    return MG_ERR_UNSUPPORTED;
+  if (occ * sms < P.nblocks) {
+    P.nblocks = occ * sms;
+    tile_plan(P);
+  }
+
+  // ---- scratch inside the static array ----
+  void* base = nullptr;
+  mg_status s = noalloc_scratch(&base);
+  if (s != MG_OK) return s;
+  char* w = (char*)base;
+  Bufs B;
+  std::memset(&B, 0, sizeof(Bufs));
+  B.psi = d_psi;
+  B.ctrl = (double*)(w + NA_CTRL);
+  B.bar = (unsigned*)(w + NA_BAR);
+  B.status = (int*)(w + NA_STATUS);
+  B.part = (double*)(w + NA_PART);
+  B.tw = (double2*)(w + NA_TW);
+  B.tabA = (double2*)(w + NA_TABA);
+  B.tabAi = (double2*)(w + NA_TABAI);
+  B.tabK = (double2*)(w + NA_TABK);
+  B.tabV = (double*)(w + NA_TABV);
+  B.tabC = (double*)(w + NA_TABC);
+  B.tabE = (double*)(w + NA_TABE);
+  B.gamma = (const double*)(w + NA_GAMMA);
+  B.scratch = nullptr;  // only the observables use it
+
+  // The array keeps the previous call's contents: the barrier words and the
+  // status word must start at zero; every other table is rewritten before use.
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double tw[2 * NOALLOC_MAXTAB], kc[NOALLOC_MAXTAB], ctrl[17];
+  for (int l = 0; l < D; ++l) {
+    const int n = P.ax[l].n;
+    for (int m = 0; m < n; ++m) {
+      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
+      tw[2 * (P.ax[l].toff + m)] = (double)std::cos(ang);
+      tw[2 * (P.ax[l].toff + m) + 1] = -(double)std::sin(ang);
+      kc[P.ax[l].toff + m] = (double)(m - n / 2);
+    }
+  }
+  for (int a = 0; a < 8; ++a) {
+    ctrl[a] = a < D ? q[a] : 0.0;
+    ctrl[8 + a] = a < D ? p[a] : 0.0;
+  }
+  ctrl[16] = 0.0;
+  s = cuda_ok(cudaMemsetAsync(w + NA_BAR, 0, 512, st));  // barrier words and status
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tw, tw, sizeof(double) * 2 * P.tab_total, cudaMemcpyHostToDevice, st));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tabC, kc, sizeof(double) * P.tab_total, cudaMemcpyHostToDevice, st));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.ctrl, ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, st));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync((void*)B.gamma, gam, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+  if (s != MG_OK) return s;
+
+  // ---- launches: A tables for the starting p-centre, then the propagation ----
+  void* targs[] = {&P, &B};
+  if (cudaLaunchKernel(init_tables_kernel(), dim3(P.nblocks), dim3(THREADS), targs, 0, st) != cudaSuccess)
+    return MG_ERR_CUDA;
+  Run R;
+  std::memset(&R, 0, sizeof(Run));
+  R.n_steps = n_steps;
+  R.S = S;
+  R.dt = dt;
+  R.split = split;
+  R.motion = grid_motion;
+  R.lead_v = split != MG_TVT;
+  R.n_units = (split == MG_TVT) ? n_steps * S + 1 : n_steps * S;
+  void* args[] = {&P, &B, &R};
+  if (cudaLaunchCooperativeKernel(fn, dim3(P.nblocks), dim3(THREADS), args, P.smem_bytes, st) != cudaSuccess)
+    return MG_ERR_CUDA;
+
+  // ---- read back the grid centres and the status (synchronises the stream) ----
+  int status = 0;
+  s = cuda_ok(cudaMemcpyAsync(ctrl, B.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, st));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(&status, B.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(st));
+  if (s != MG_OK) return s;
+  if (status != 0) return (mg_status)status;
+  for (int a = 0; a < D; ++a) {
+    q[a] = ctrl[a];
+    p[a] = ctrl[8 + a];
+  }
+  return MG_OK;
+}
