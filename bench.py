@@ -200,15 +200,35 @@ def cpu_baseline_and_error(mgmod, torch):
     return cpu, err
 
 
+def run_profile(args):
+    """A short run of the same workload for profiler captures: the propagate
+    kernel is launched warmup + steps times, 10 time steps per launch."""
+    import torch
+    import paper_1909_06412_gb300 as mg
+
+    fac, qc, pc = initial(mg)
+    g = mg.Propagator(N_GRID, DQ, minv=MINV)
+    g.set_potential(mg.MG_POT_ATOM_DIATOM, POT)
+    g.set_separable(fac, qc, pc)
+    for _ in range(args.warmup + args.steps):
+        g.propagate(10, DT, SCHEME)
+    g.sync()
+    print(json.dumps({"profile_run": True, "launches": g.launches}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up and timed propagate calls of 10 steps (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     import torch
     import paper_1909_06412_gb300 as mg

@@ -30,7 +30,7 @@ constexpr int CHUNK_REGION = 64 * 1024;  // bytes per smem region otherwise
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, scratch, total;
+  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, scratch, total;
 };
 
 Layout layout_for(int D, const int64_t* N) {
@@ -58,6 +58,7 @@ Layout layout_for(int D, const int64_t* N) {
   L.tabC = put(tt * sizeof(double));
   L.tabE = put(tt * sizeof(double));
   L.gamma = put(MAX_STAGES * sizeof(double));
+  L.sct = put(256 * sizeof(double2));
   L.scratch = put((size_t)npts * sizeof(double2));
   L.total = o;
   return L;
@@ -71,23 +72,32 @@ bool axis_supported(int64_t n) {
   return n == 1;
 }
 
-void radix_plan(int n, AxisPlan& ax) {
+// Radix passes for length n using powers of two no larger than rmax (8, 4 or 2)
+// and radix 3.  A smaller rmax gives more butterflies per pass: on GB300 an
+// FP64 warp instruction costs a sub-partition 64 cycles whatever its number of
+// active lanes, so a CTA with few lines is faster with radix 4 or 2 spread over
+// all four sub-partitions than with radix 8 on one or two.
+void radix_plan(int n, AxisPlan& ax, int rmax = 8) {
   int c2 = 0, c3 = 0;
   while (n % 2 == 0) { n /= 2; ++c2; }
   while (n % 3 == 0) { n /= 3; ++c3; }
   ax.nrad = 0;
-  while (c2 >= 3) { ax.rad[ax.nrad++] = 8; c2 -= 3; }
-  if (c2 == 2) ax.rad[ax.nrad++] = 4;
-  if (c2 == 1) ax.rad[ax.nrad++] = 2;
+  if (rmax >= 8)
+    while (c2 >= 3) { ax.rad[ax.nrad++] = 8; c2 -= 3; }
+  if (rmax >= 4)
+    while (c2 >= 2) { ax.rad[ax.nrad++] = 4; c2 -= 2; }
+  while (c2 >= 1) { ax.rad[ax.nrad++] = 2; c2 -= 1; }
   for (int i = 0; i < c3; ++i) ax.rad[ax.nrad++] = 3;
 }
 
 size_t smem_for(const Plan& P) {
+  // must match carve() in mg_kernels.cu
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-  size_t s = 3 * r16(vs * P.maxn) + r16(sizeof(double) * NVCOL * P.tab_total) +
-             2 * r16(sizeof(double) * P.tab_total) + r16(sizeof(double) * (THREADS / 32) * PSTRIDE) +
-             r16(sizeof(double) * PSTRIDE) + 2 * r16((size_t)P.region_bytes);
+  const size_t TT = (size_t)P.tab_total;
+  size_t s = 4 * r16(vs * TT) + r16(sizeof(double) * NVCOL * TT) + 2 * r16(sizeof(double) * TT) +
+             r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (P.D + 2)) +
+             r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * 40) + 2 * r16((size_t)P.region_bytes);
   return s;
 }
 
@@ -117,6 +127,11 @@ void tile_plan(Plan& P) {
     AxisPlan& ax = P.ax[l];
     const int64_t tile_bytes = (int64_t)ax.W * ax.n * vs;
     ax.tpc = (int)std::max<int64_t>(1, P.region_bytes / tile_bytes);
+    // butterflies a CTA has per pass; aim for at least one warp per sub-partition
+    const int64_t mine = (ax.ntiles + P.nblocks - 1) / P.nblocks;
+    const int64_t lines = std::min<int64_t>(mine, ax.tpc) * ax.W;
+    const int rmax = lines * ax.n / 8 >= 128 ? 8 : (lines * ax.n / 4 >= 128 ? 4 : 2);
+    radix_plan(ax.n, ax, rmax);
   }
   P.smem_bytes = (int)smem_for(P);
 }
@@ -150,6 +165,15 @@ bool scheme_coeffs(const char* name, std::vector<double>& g) {
     g.swap(next);
   }
   return (int)g.size() <= MAX_STAGES;
+}
+
+// e^{i k pi/128}, k = 0..255, for the table-driven sincos of the kernels.
+void fill_sincos_table(double* t) {
+  for (int k = 0; k < 256; ++k) {
+    const long double a = 3.14159265358979323846264338327950288L * (long double)k / 128.0L;
+    t[2 * k] = (double)std::cos(a);
+    t[2 * k + 1] = (double)std::sin(a);
+  }
 }
 
 // ---- digamma by recurrence + asymptotic series (Abramowitz & Stegun 6.3.5,
@@ -208,7 +232,7 @@ mg_status launch_plain(mg_ctx* c, void* fn, void** args, size_t smem) {
 
 mg_status init_tables(mg_ctx* c) {
   void* args[] = {&c->P, &c->B};
-  return launch_plain(c, init_tables_kernel(), args, 0);
+  return launch_plain(c, init_tables_kernel(), args, c->P.smem_bytes);
 }
 
 mg_status read_status(mg_ctx* c) {
@@ -350,6 +374,7 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
   B.tabC = (double*)(w + L.tabC);
   B.tabE = (double*)(w + L.tabE);
   B.gamma = (const double*)(w + L.gamma);
+  B.sct = (double2*)(w + L.sct);
   B.scratch = (double2*)(w + L.scratch);
 
   // static tables: twiddles e^{-2 pi i m/N_l} and k - N_l/2
@@ -363,7 +388,10 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
       kc[P.ax[l].toff + m] = (double)(m - n / 2);
     }
   }
+  std::vector<double> sct(512);
+  fill_sincos_table(sct.data());
   mg_status s = cuda_ok(cudaMemsetAsync(d_work, 0, L.scratch, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.sct, sct.data(), 512 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tabC, kc.data(), kc.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
@@ -594,7 +622,7 @@ mg_status mg_get_observables(mg_ctx* c, double* norm, double* energy, double* me
   if (s != MG_OK) return s;
   const Plan& P = c->P;
   void* targs[] = {&c->P, &c->B};
-  s = launch_plain(c, obs_tables_kernel(), targs, 0);
+  s = launch_plain(c, obs_tables_kernel(), targs, P.smem_bytes);
   void* fn = obs_kernel(P.prec, P.pot_kind);
   for (int l = P.D - 1; l >= 0 && s == MG_OK; --l) {
     int mode = 0;
@@ -667,21 +695,29 @@ constexpr int NOALLOC_MAXDEV = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Offsets inside g_noalloc_scratch (fixed, independent of the grid).
+// Offsets inside g_noalloc_scratch (fixed, independent of the grid), each
+// aligned to 256 bytes (the kernels load double2 values: 16-byte alignment
+// is required).
+constexpr size_t na_al(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t NA_CTRL = 0;
 constexpr size_t NA_BAR = 256;
 constexpr size_t NA_STATUS = 512;
 constexpr size_t NA_PART = 768;
-constexpr size_t NA_TW = NA_PART + 2ull * NOALLOC_MAXBLOCKS * PSTRIDE * sizeof(double);
-constexpr size_t NA_TABA = NA_TW + NOALLOC_MAXTAB * sizeof(double2);
-constexpr size_t NA_TABAI = NA_TABA + NOALLOC_MAXTAB * sizeof(double2);
-constexpr size_t NA_TABK = NA_TABAI + NOALLOC_MAXTAB * sizeof(double2);
-constexpr size_t NA_TABV = NA_TABK + NOALLOC_MAXTAB * sizeof(double2);
-constexpr size_t NA_TABC = NA_TABV + (size_t)NVCOL * NOALLOC_MAXTAB * sizeof(double);
-constexpr size_t NA_TABE = NA_TABC + NOALLOC_MAXTAB * sizeof(double);
-constexpr size_t NA_GAMMA = NA_TABE + NOALLOC_MAXTAB * sizeof(double);
-constexpr size_t NA_END = NA_GAMMA + MAX_STAGES * sizeof(double);
+constexpr size_t NA_TW = na_al(NA_PART + 2ull * NOALLOC_MAXBLOCKS * PSTRIDE * sizeof(double));
+constexpr size_t NA_TABA = na_al(NA_TW + NOALLOC_MAXTAB * sizeof(double2));
+constexpr size_t NA_TABAI = na_al(NA_TABA + NOALLOC_MAXTAB * sizeof(double2));
+constexpr size_t NA_TABK = na_al(NA_TABAI + NOALLOC_MAXTAB * sizeof(double2));
+constexpr size_t NA_TABV = na_al(NA_TABK + NOALLOC_MAXTAB * sizeof(double2));
+constexpr size_t NA_TABC = na_al(NA_TABV + (size_t)NVCOL * NOALLOC_MAXTAB * sizeof(double));
+constexpr size_t NA_TABE = na_al(NA_TABC + NOALLOC_MAXTAB * sizeof(double));
+constexpr size_t NA_GAMMA = na_al(NA_TABE + NOALLOC_MAXTAB * sizeof(double));
+constexpr size_t NA_SCT = na_al(NA_GAMMA + MAX_STAGES * sizeof(double));
+constexpr size_t NA_END = NA_SCT + 256 * sizeof(double2);
 static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "static scratch too small for its layout");
+static_assert(NA_TW % 256 == 0 && NA_TABA % 256 == 0 && NA_TABAI % 256 == 0 && NA_TABK % 256 == 0 &&
+                  NA_TABV % 256 == 0 && NA_TABC % 256 == 0 && NA_TABE % 256 == 0 && NA_GAMMA % 256 == 0 &&
+                  NA_SCT % 256 == 0,
+              "static scratch regions must be 256-byte aligned");
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[NOALLOC_MAXDEV];
@@ -848,12 +884,14 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   B.tabC = (double*)(w + NA_TABC);
   B.tabE = (double*)(w + NA_TABE);
   B.gamma = (const double*)(w + NA_GAMMA);
+  B.sct = (double2*)(w + NA_SCT);
   B.scratch = nullptr;  // only the observables use it
 
   // The array keeps the previous call's contents: the barrier words and the
   // status word must start at zero; every other table is rewritten before use.
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  double tw[2 * NOALLOC_MAXTAB], kc[NOALLOC_MAXTAB], ctrl[17];
+  double tw[2 * NOALLOC_MAXTAB], kc[NOALLOC_MAXTAB], ctrl[17], sct[512];
+  fill_sincos_table(sct);
   for (int l = 0; l < D; ++l) {
     const int n = P.ax[l].n;
     for (int m = 0; m < n; ++m) {
@@ -873,11 +911,15 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.tabC, kc, sizeof(double) * P.tab_total, cudaMemcpyHostToDevice, st));
   if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.ctrl, ctrl, sizeof(ctrl), cudaMemcpyHostToDevice, st));
   if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync((void*)B.gamma, gam, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpyAsync(B.sct, sct, sizeof(sct), cudaMemcpyHostToDevice, st));
   if (s != MG_OK) return s;
 
   // ---- launches: A tables for the starting p-centre, then the propagation ----
   void* targs[] = {&P, &B};
-  if (cudaLaunchKernel(init_tables_kernel(), dim3(P.nblocks), dim3(THREADS), targs, 0, st) != cudaSuccess)
+  if (P.smem_bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(init_tables_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes) != cudaSuccess)
+    return MG_ERR_CUDA;
+  if (cudaLaunchKernel(init_tables_kernel(), dim3(P.nblocks), dim3(THREADS), targs, P.smem_bytes, st) != cudaSuccess)
     return MG_ERR_CUDA;
   Run R;
   std::memset(&R, 0, sizeof(Run));

@@ -138,10 +138,16 @@ template <bool INV, typename V> struct Dft<INV, 8, V> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Stockham FFT in shared memory
+// ---------------------------------------------------------------------------
+
 // One Stockham autosort pass of radix R over L lines of length n (in -> out).
+// The first pass (Ns == 1) has no twiddles; it applies the diagonal
+// pre-multiplier `pre` (A_l or K_l) to its inputs instead, if given.
 template <bool INV, int R, typename V>
-__device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __restrict__ out, int n,
-                                              int L, int Ns, const V* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __restrict__ out, int n, int L,
+                                              int Ns, const V* __restrict__ tw, const V* __restrict__ pre) {
   const int nR = n / R;
   const int total = L * nR;
   const int ts = n / (Ns * R);
@@ -160,6 +166,9 @@ __device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __res
         const V w = tw[k * r * ts];
         v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
       }
+    } else if (pre) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = cmul(v[r], pre[j + r * nR]);
     }
     Dft<INV, R, V>::run(v);
     const int base = (j - k) * R + k;
@@ -170,14 +179,15 @@ __device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __res
 
 // Full 1D transform of L lines; returns the buffer that holds the result.
 template <bool INV, typename V>
-__device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw) {
+__device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw, const V* pre) {
   int Ns = 1;
   for (int pi = 0; pi < ax.nrad; ++pi) {
     const int R = ax.rad[pi];
-    if (R == 8) stockham_pass<INV, 8>(in, out, ax.n, L, Ns, tw);
-    else if (R == 4) stockham_pass<INV, 4>(in, out, ax.n, L, Ns, tw);
-    else if (R == 3) stockham_pass<INV, 3>(in, out, ax.n, L, Ns, tw);
-    else stockham_pass<INV, 2>(in, out, ax.n, L, Ns, tw);
+    const V* pm = pi == 0 ? pre : nullptr;
+    if (R == 8) stockham_pass<INV, 8>(in, out, ax.n, L, Ns, tw, pm);
+    else if (R == 4) stockham_pass<INV, 4>(in, out, ax.n, L, Ns, tw, pm);
+    else if (R == 3) stockham_pass<INV, 3>(in, out, ax.n, L, Ns, tw, pm);
+    else stockham_pass<INV, 2>(in, out, ax.n, L, Ns, tw, pm);
     __syncthreads();
     V* t = in;
     in = out;
@@ -185,6 +195,31 @@ __device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw) {
     Ns *= R;
   }
   return in;
+}
+
+// ---------------------------------------------------------------------------
+// e^{i theta} by the table-driven method (Tang 1990): theta = k pi/128 + r with
+// a Cody-Waite reduction (pi/128 split in three words), e^{i k pi/128} from a
+// 256-entry table, and Taylor series of sin r, cos r for |r| <= pi/256
+// (truncation below 1e-17).  About 17 FP64 instructions instead of ~27.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void expi_tab(double th, const double2* __restrict__ tab, double& s, double& c) {
+  if (!(fabs(th) < 1e15)) {  // huge or non-finite argument: library routine
+    sincos(th, &s, &c);
+    return;
+  }
+  const long long ki = __double2ll_rn(th * 40.74366543152521);  // 128/pi
+  const double k = (double)ki;
+  double r = fma(-k, 0.02454369260617026, th);
+  r = fma(-k, 9.567553118338697e-19, r);
+  r = fma(-k, -2.3396639138424529e-35, r);
+  const double2 t = tab[ki & 255];
+  const double r2 = r * r;
+  const double sr = fma(r2 * r, fma(r2, 1.0 / 120.0, -1.0 / 6.0), r);
+  const double cr = fma(r2, fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  c = fma(t.x, cr, -t.y * sr);
+  s = fma(t.y, cr, t.x * sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,7 +259,7 @@ __device__ bool grid_sync(const Bufs& B, int* sflag) {
       const uint64_t t0 = global_ns();
       unsigned spins = 0;
       while (ld_acquire_u32(gen) == g0) {
-        __nanosleep(32);
+        if (spins > 64) __nanosleep(20);
         ++spins;
         if ((spins & 127u) == 0 && (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS)) {
           ok = 0;
@@ -241,18 +276,26 @@ __device__ bool grid_sync(const Bufs& B, int* sflag) {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout
+// Shared memory: every per-axis table of all axes, the scalar state of the
+// grid centres, reduction scratch and two data regions.
 // ---------------------------------------------------------------------------
 
+// scalar slots (doubles) in Smem::sc
+enum { SC_Q = 0, SC_P = 8, SC_QN = 16, SC_DELTA = 24, SC_TAU = 32, SC_SIG = 33, SC_SGH = 34, SC_HASV = 35,
+       SC_ERR = 36, SC_N = 40 };
+
 template <typename V> struct Smem {
-  V* tw;        // maxn twiddles of the current axis
-  V* tpre;      // maxn pre-multipliers
-  V* tpost;     // maxn post-multipliers
+  V* tw;        // twiddles, all axes (tab_total)
+  V* tA;        // A_l
+  V* tAi;       // conj(A_l)/N_l
+  V* tK;        // kinetic multiplier
   double* tv;   // NVCOL * tab_total potential columns
-  double* tc;   // tab_total values k - N/2
-  double* te;   // tab_total kinetic-energy values
-  double* red;  // (THREADS/32) * PSTRIDE
+  double* tc;   // k - N/2
+  double* te;   // kinetic energy per axis entry
+  double2* sct; // 256-entry e^{i k pi/128}
+  double* red;  // THREADS * (D+2) per-thread partials
   double* fin;  // PSTRIDE finished sums
+  double* sc;   // SC_N scalars
   V* reg[2];    // data regions
 };
 
@@ -264,17 +307,42 @@ template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* bas
     off += (bytes + 15) & ~size_t(15);
     return p;
   };
-  s.tw = (V*)take(sizeof(V) * P.maxn);
-  s.tpre = (V*)take(sizeof(V) * P.maxn);
-  s.tpost = (V*)take(sizeof(V) * P.maxn);
-  s.tv = (double*)take(sizeof(double) * NVCOL * P.tab_total);
-  s.tc = (double*)take(sizeof(double) * P.tab_total);
-  s.te = (double*)take(sizeof(double) * P.tab_total);
-  s.red = (double*)take(sizeof(double) * (THREADS / 32) * PSTRIDE);
+  const int TT = P.tab_total;
+  s.tw = (V*)take(sizeof(V) * TT);
+  s.tA = (V*)take(sizeof(V) * TT);
+  s.tAi = (V*)take(sizeof(V) * TT);
+  s.tK = (V*)take(sizeof(V) * TT);
+  s.tv = (double*)take(sizeof(double) * NVCOL * TT);
+  s.tc = (double*)take(sizeof(double) * TT);
+  s.te = (double*)take(sizeof(double) * TT);
+  s.sct = (double2*)take(sizeof(double2) * 256);
+  s.red = (double*)take(sizeof(double) * THREADS * (P.D + 2));
   s.fin = (double*)take(sizeof(double) * PSTRIDE);
+  s.sc = (double*)take(sizeof(double) * SC_N);
   s.reg[0] = (V*)take(P.region_bytes);
   s.reg[1] = (V*)take(P.region_bytes);
   return s;
+}
+
+enum { LT_TW = 1, LT_A = 2, LT_K = 4, LT_V = 8, LT_C = 16, LT_E = 32, LT_SCT = 64 };
+
+// Copy tables from global memory (written by other CTAs) into shared memory.
+template <typename V> __device__ void load_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
+  const int TT = P.tab_total;
+  for (int e = threadIdx.x; e < TT; e += blockDim.x) {
+    if (what & LT_TW) S.tw[e] = from_d2<V>(__ldcg(B.tw + e));
+    if (what & LT_A) {
+      S.tA[e] = from_d2<V>(__ldcg(B.tabA + e));
+      S.tAi[e] = from_d2<V>(__ldcg(B.tabAi + e));
+    }
+    if (what & LT_K) S.tK[e] = from_d2<V>(__ldcg(B.tabK + e));
+    if (what & LT_V)
+      for (int c = 0; c < NVCOL; ++c) S.tv[c * TT + e] = __ldcg(B.tabV + c * TT + e);
+    if (what & LT_C) S.tc[e] = __ldcg(B.tabC + e);
+    if (what & LT_E) S.te[e] = __ldcg(B.tabE + e);
+  }
+  if (what & LT_SCT)
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) S.sct[e] = __ldcg(B.sct + e);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,9 +387,9 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
   } else if (KIND == POT_ATOM_DIATOM) {
     const double gR = COL(0, 0), dgR = COL(1, 0), sgR = COL(2, 0);
     const double sf = COL(0, 1), df = COL(1, 1), h = COL(2, 1), dh = COL(3, 1);
-    th = sf + sgR * h;
+    th = fma(sgR, h, sf);
     g[0] = dgR * h;
-    g[1] = df + gR * dh;
+    g[1] = fma(gR, dh, df);
   } else if (KIND == POT_HENON_HEILES) {
     const double lam = P.pot[0];
     double x[MAXD], x2[MAXD];
@@ -337,14 +405,14 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
 #pragma unroll
     for (int a = 0; a + 1 < MAXD; ++a)
       if (a + 1 < D) {
-        cpl += x2[a] * x[a + 1];
-        g[a] += 2.0 * lam * x[a] * x[a + 1];
-        g[a + 1] += lam * x2[a];
+        cpl = fma(x2[a], x[a + 1], cpl);
+        g[a] = fma(2.0 * lam * x[a], x[a + 1], g[a]);
+        g[a + 1] = fma(lam, x2[a], g[a + 1]);
       }
-    th = s1 + sgh * lam * cpl;
+    th = fma(sgh * lam, cpl, s1);
   } else {  // POT_SECREST_JOHNSON
     const double c = COL(0, 1);
-    th = COL(0, 0) + COL(2, 0) * c;
+    th = fma(COL(2, 0), c, COL(0, 0));
     const double e = COL(3, 0) * c;
     g[0] = COL(1, 0) + e;
     g[1] = -e;
@@ -404,36 +472,51 @@ __device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, d
 
 enum { TB_K = 1, TB_V = 2, TB_A = 4, TB_E = 8 };
 
-// Distributed construction of the per-axis tables: every thread of the grid
-// builds at most a few entries.  A grid barrier must follow before use.
-__device__ void build_tables(const Plan& P, const Bufs& B, int what, double tau, const double* delta,
-                             const double* p, const double* q, double sgh) {
-  const int D = P.D;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.tab_total; e += gridDim.x * blockDim.x) {
+// Distributed construction of the per-axis tables.  The work is cut into
+// tasks of 32 consecutive entries of one table, one task per warp with every
+// lane busy (an FP64 warp instruction costs the same with 1 or 32 lanes), and
+// the tasks are dealt out first to warp 0 of every CTA, then to warp 1, ...
+// so that they run on as many SM sub-partitions as possible at once.  Inputs
+// (tau, delta, p, q, sgh) come from the CTA's scalar slots.  A grid barrier
+// must follow before the tables are used.
+template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
+  const int TT = P.tab_total, D = P.D;
+  const int nch = (TT + 31) / 32;
+  int kinds[4], nk = 0;
+  if (what & TB_K) kinds[nk++] = TB_K;
+  if (what & TB_V) kinds[nk++] = TB_V;
+  if (what & TB_A) kinds[nk++] = TB_A;
+  if (what & TB_E) kinds[nk++] = TB_E;
+  const int ntask = nk * nch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int t = warp * gridDim.x + blockIdx.x; t < ntask; t += nwarps * gridDim.x) {
+    const int kind = kinds[t / nch];
+    const int e = (t % nch) * 32 + lane;
+    if (e >= TT) continue;
     int a = 0;
     while (a + 1 < D && e >= P.ax[a + 1].toff) ++a;
     const int j = e - P.ax[a].toff;
     const int n = P.ax[a].n;
     const double c = (double)(j - n / 2);
-    if (what & TB_K) {
-      const double pk = p[a] + c * P.dp[a];
-      const double th = (delta[a] * pk - 0.5 * tau * P.minv[a] * pk * pk) / P.hbar;
-      double s, co;
-      sincos(th, &s, &co);
-      __stcg(B.tabK + e, make_double2(co, s));
-    }
-    if (what & TB_A) {
-      const double th = -p[a] * c * P.dq[a] / P.hbar;
-      double s, co;
-      sincos(th, &s, &co);
+    const double* sc = S.sc;
+    if (kind == TB_K) {
+      const double pk = fma(c, P.dp[a], sc[SC_P + a]);
+      const double th = (sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk) / P.hbar;
+      double sn, cs;
+      expi_tab(th, S.sct, sn, cs);
+      __stcg(B.tabK + e, make_double2(cs, sn));
+    } else if (kind == TB_A) {
+      const double th = -sc[SC_P + a] * c * P.dq[a] / P.hbar;
+      double sn, cs;
+      expi_tab(th, S.sct, sn, cs);
       const double sg = (j & 1) ? -1.0 : 1.0;
-      __stcg(B.tabA + e, make_double2(sg * co, sg * s));
+      __stcg(B.tabA + e, make_double2(sg * cs, sg * sn));
       // conj(A)/N by division: a rounded 1/N would bias every inverse transform
-      __stcg(B.tabAi + e, make_double2(sg * co / (double)n, -sg * s / (double)n));
-    }
-    if (what & TB_V) vcolumns(P, B, e, a, q[a] + c * P.dq[a], sgh);
-    if (what & TB_E) {
-      const double pk = p[a] + c * P.dp[a];
+      __stcg(B.tabAi + e, make_double2(sg * cs / (double)n, -sg * sn / (double)n));
+    } else if (kind == TB_V) {
+      vcolumns(P, B, e, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH]);
+    } else {
+      const double pk = fma(c, P.dp[a], sc[SC_P + a]);
       __stcg(B.tabE + e, 0.5 * P.minv[a] * pk * pk);
     }
   }
@@ -449,35 +532,35 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Per-thread partials -> one record per CTA.  The per-thread values go
+// through shared memory so that warp v sums value v (8 partials per lane, then
+// a shuffle tree): nv short FP64 chains on different sub-partitions instead of
+// nv * 8 warps of shuffle trees.
 template <typename V>
 __device__ void block_partials(const Bufs& B, const Smem<V>& S, int slot, const double* acc, int nv) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = blockDim.x;
 #pragma unroll
   for (int v = 0; v < MAXD + 2; ++v)
-    if (v < nv) {
-      const double x = warp_sum(acc[v]);
-      if (lane == 0) S.red[warp * PSTRIDE + v] = x;
-    }
+    if (v < nv) S.red[v * nt + threadIdx.x] = acc[v];
   __syncthreads();
-  if (threadIdx.x < nv) {
+  for (int v = warp; v < nv; v += nt >> 5) {
     double s = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += S.red[w * PSTRIDE + threadIdx.x];
-    __stcg(B.part + ((size_t)slot * gridDim.x + blockIdx.x) * PSTRIDE + threadIdx.x, s);
+    for (int k = lane; k < nt; k += 32) s += S.red[v * nt + k];
+    s = warp_sum(s);
+    if (lane == 0) __stcg(B.part + ((size_t)slot * gridDim.x + blockIdx.x) * PSTRIDE + v, s);
   }
   __syncthreads();
 }
 
 // Sum the per-CTA partials of `slot` in a fixed order; result in S.fin.
 template <typename V> __device__ void finish(const Bufs& B, const Smem<V>& S, int slot, int nv) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int v = 0; v < nv; ++v) {
-      double s = 0;
-      for (int b = lane; b < (int)gridDim.x; b += 32)
-        s += __ldcg(B.part + ((size_t)slot * gridDim.x + b) * PSTRIDE + v);
-      s = warp_sum(s);
-      if (lane == 0) S.fin[v] = s;
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = warp; v < nv; v += blockDim.x >> 5) {
+    double s = 0;
+    for (int b = lane; b < (int)gridDim.x; b += 32)
+      s += __ldcg(B.part + ((size_t)slot * gridDim.x + b) * PSTRIDE + v);
+    s = warp_sum(s);
+    if (lane == 0) S.fin[v] = s;
   }
   __syncthreads();
 }
@@ -497,10 +580,8 @@ struct PassArgs {
   int pre, post;  // multipliers (post: conj(A)/N)
   int red;        // fused reduction / potential phase
   int slot;       // partial-sum slot
-  double sgh;     // -sigma/hbar (general harmonic only; else folded in tables)
   const void* src;
   void* dst;
-  const double* q;  // grid centre (RED_OBS_V)
 };
 
 // Multi-index of element j of line (o, i) of axis l.
@@ -529,22 +610,10 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   const int64_t tpo = contig ? 1 : s / W;  // tiles per outer index
   const int64_t ws = contig ? n : 1;       // element step between lines of a tile
   const int64_t es = contig ? 1 : s;       // element step along the axis
-
-  // tables of this pass
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    if (A.fft) S.tw[j] = from_d2<V>(__ldcg(B.tw + ax.toff + j));
-    if (A.pre) S.tpre[j] = from_d2<V>(__ldcg((A.pre == PRE_A ? B.tabA : B.tabK) + ax.toff + j));
-    if (A.post) S.tpost[j] = from_d2<V>(__ldcg(B.tabAi + ax.toff + j));
-  }
-  if (A.red != RED_NONE) {
-    for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
-      S.tc[e] = __ldcg(B.tabC + e);
-      if (A.red == RED_OBS_KIN) S.te[e] = __ldcg(B.tabE + e);
-      if (A.red == RED_V || A.red == RED_OBS_V)
-        for (int c = 0; c < NVCOL; ++c) S.tv[c * P.tab_total + e] = __ldcg(B.tabV + c * P.tab_total + e);
-    }
-  }
-  __syncthreads();
+  const V* tw = S.tw + ax.toff;
+  const V* pre = A.pre == PRE_A ? S.tA + ax.toff : (A.pre == PRE_K ? S.tK + ax.toff : nullptr);
+  const V* post = A.post ? S.tAi + ax.toff : nullptr;
+  const double sgh = S.sc[SC_SGH];
 
   double acc[MAXD + 2];
 #pragma unroll
@@ -562,11 +631,6 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
     V* cur;
     if (A.from_smem) {
       cur = S.reg[res_in];
-      if (A.pre)
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-          const int j = e % n;
-          cur[e] = cmul(cur[e], S.tpre[j]);
-        }
     } else {
       cur = S.reg[0];
       for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -578,13 +642,16 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
         const int64_t t = bid + (c0 + ti) * nb;
         const int64_t o = t / tpo;
         const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
-        V v = __ldcg(src + base + j * es + w * ws);
-        if (A.pre) v = cmul(v, S.tpre[j]);
-        cur[(ti * W + w) * n + j] = v;
+        cur[(ti * W + w) * n + j] = __ldcg(src + base + j * es + w * ws);
       }
     }
     __syncthreads();
-    if (A.fft) cur = stockham<INV>(cur, cur == S.reg[0] ? S.reg[1] : S.reg[0], nt * W, ax, S.tw);
+    if (A.fft) {
+      cur = stockham<INV>(cur, cur == S.reg[0] ? S.reg[1] : S.reg[0], nt * W, ax, tw, pre);
+    } else if (pre) {
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) cur[e] = cmul(cur[e], pre[e % n]);
+      __syncthreads();
+    }
 
     // epilogue
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -597,39 +664,39 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
       const int64_t o = t / tpo;
       const int si = (ti * W + w) * n + j;
       V v = cur[si];
-      if (A.post) v = cmul(v, S.tpost[j]);
+      if (post) v = cmul(v, post[j]);
       if (A.red != RED_NONE) {
         int idx[MAXD];
         const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
         const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
         decode(P, A.l, lo, li, j, idx);
         const double2 d = to_d2(v);
-        const double w2 = d.x * d.x + d.y * d.y;
+        const double w2 = fma(d.x, d.x, d.y * d.y);
         acc[0] += w2;
         if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
           double te = 0;
 #pragma unroll
           for (int a = 0; a < MAXD; ++a)
             if (a < D) {
-              acc[1 + a] += S.tc[P.ax[a].toff + idx[a]] * w2;
+              acc[1 + a] = fma(S.tc[P.ax[a].toff + idx[a]], w2, acc[1 + a]);
               if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
             }
-          if (A.red == RED_OBS_KIN) acc[D + 1] += te * w2;
+          if (A.red == RED_OBS_KIN) acc[D + 1] = fma(te, w2, acc[D + 1]);
         } else {
           double th, g[MAXD];
-          vpoint<KIND>(P, S.tv, idx, A.sgh, th, g);
+          vpoint<KIND>(P, S.tv, idx, sgh, th, g);
           if (A.red == RED_V) {
 #pragma unroll
             for (int a = 0; a < MAXD; ++a)
-              if (a < D) acc[1 + a] += g[a] * w2;
+              if (a < D) acc[1 + a] = fma(g[a], w2, acc[1 + a]);
             double sn, cs;
-            sincos(th, &sn, &cs);
-            v = from_d2<V>(make_double2(d.x * cs - d.y * sn, d.x * sn + d.y * cs));
+            expi_tab(th, S.sct, sn, cs);
+            v = from_d2<V>(make_double2(fma(d.x, cs, -d.y * sn), fma(d.x, sn, d.y * cs)));
           } else {  // observables: <x> and <V>
 #pragma unroll
             for (int a = 0; a < MAXD; ++a)
-              if (a < D) acc[1 + a] += (A.q[a] + S.tc[P.ax[a].toff + idx[a]] * P.dq[a]) * w2;
-            acc[D + 1] += th * w2;
+              if (a < D) acc[1 + a] = fma(fma(S.tc[P.ax[a].toff + idx[a]], P.dq[a], S.sc[SC_Q + a]), w2, acc[1 + a]);
+            acc[D + 1] = fma(th, w2, acc[D + 1]);
           }
         }
       }
@@ -669,7 +736,9 @@ template <typename T> __device__ void flush_resident(const Plan& P, const Bufs& 
 }
 
 // ---------------------------------------------------------------------------
-// The persistent propagation kernel
+// Scalar bookkeeping of the grid centres.  Runs in warp 0 only, lane a for
+// axis a, results in shared memory (every extra warp running scalar FP64
+// code would cost another 64 cycles per instruction on its sub-partition).
 // ---------------------------------------------------------------------------
 
 // Substep sizes of kinetic unit u (a kinetic substep, optionally followed by a
@@ -699,6 +768,54 @@ __device__ __forceinline__ void unit_coeffs(const Run& R, const double* gam, int
   }
 }
 
+// After the kinetic moments: delta = tau m^-1 <p> (or m^-1 p, or 0), q_new.
+template <typename V> __device__ void centre_after_kinetic(const Plan& P, const Smem<V>& S, int motion) {
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x;
+    double* sc = S.sc;
+    int bad = 0;
+    if (a < P.D) {
+      const double n = S.fin[0];
+      const double pi = fma(P.dp[a], S.fin[1 + a] / n, sc[SC_P + a]);
+      const double mom = motion == GRID_ADAPTIVE ? pi : sc[SC_P + a];
+      const double delta = motion == GRID_FIXED ? 0.0 : sc[SC_TAU] * P.minv[a] * mom;
+      if (!(n > 0) || !isfinite(n) || !isfinite(pi)) bad = ST_NONFINITE;
+      else if (fabs(delta) > 10.0 * P.N[a] * P.dq[a]) bad = ST_UNSTABLE;
+      sc[SC_DELTA + a] = delta;
+      sc[SC_QN + a] = sc[SC_Q + a] + delta;
+    }
+    bad = __reduce_min_sync(0xffffffffu, bad);
+    if (a == 0) sc[SC_ERR] = (double)bad;
+  }
+  __syncthreads();
+}
+
+// After the potential moments: p <- p - sigma <dV/dq>.
+template <typename V> __device__ void centre_after_potential(const Plan& P, const Smem<V>& S, int motion) {
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x;
+    double* sc = S.sc;
+    int bad = 0;
+    if (a < P.D) {
+      const double n = S.fin[0];
+      const double g = S.fin[1 + a] / n;
+      if (!(n > 0) || !isfinite(n) || !isfinite(g)) bad = ST_NONFINITE;
+      if (motion != GRID_FIXED) {
+        const double dpn = sc[SC_SIG] * g;
+        if (fabs(dpn) > 10.0 * P.N[a] * P.dp[a]) bad = bad ? bad : ST_UNSTABLE;
+        sc[SC_P + a] -= dpn;
+      }
+    }
+    bad = __reduce_min_sync(0xffffffffu, bad);
+    if (a == 0) sc[SC_ERR] = (double)bad;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The persistent propagation kernel
+// ---------------------------------------------------------------------------
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
     k_propagate(const __grid_constant__ Plan P, const __grid_constant__ Bufs B, const __grid_constant__ Run RN) {
@@ -709,50 +826,58 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int D = P.D;
   // an unreported error from an earlier launch makes every later launch a no-op
   if (__ldcg(B.status) != ST_OK) return;
-  double q[MAXD], p[MAXD], qn[MAXD], delta[MAXD];
-#pragma unroll
-  for (int a = 0; a < MAXD; ++a) {
-    q[a] = a < D ? __ldcg(B.ctrl + a) : 0.0;
-    p[a] = a < D ? __ldcg(B.ctrl + 8 + a) : 0.0;
-    qn[a] = q[a];
-    delta[a] = 0.0;
+  double* sc = S.sc;
+  if (threadIdx.x < SC_N) sc[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < D) {
+    sc[SC_Q + threadIdx.x] = __ldcg(B.ctrl + threadIdx.x);
+    sc[SC_P + threadIdx.x] = __ldcg(B.ctrl + 8 + threadIdx.x);
   }
+  load_tables(P, B, S, LT_TW | LT_A | LT_C | LT_SCT);
+  __syncthreads();
   const double* gam = B.gamma;
   int res = -1;
   bool kept = false;
-  int err = ST_OK;
 
   if (RN.lead_v) {
-    const double sig = (RN.split == SPLIT_VTV ? 0.5 : 1.0) * gam[0] * RN.dt;
-    const double sgh = -sig / P.hbar;
-    build_tables(P, B, TB_V, 0.0, delta, p, q, sgh);
+    if (threadIdx.x == 0) {
+      const double sig = (RN.split == SPLIT_VTV ? 0.5 : 1.0) * gam[0] * RN.dt;
+      sc[SC_SIG] = sig;
+      sc[SC_SGH] = -sig / P.hbar;
+    }
+    if (threadIdx.x < D) sc[SC_QN + threadIdx.x] = sc[SC_Q + threadIdx.x];
+    __syncthreads();
+    build_tables(P, B, S, TB_V);
     if (!grid_sync(B, &sflag)) return;
+    load_tables(P, B, S, LT_V);
+    __syncthreads();
     PassArgs a{};
-    a.l = D - 1; a.fft = 0; a.red = RED_V; a.slot = 1; a.sgh = sgh;
+    a.l = D - 1; a.fft = 0; a.red = RED_V; a.slot = 1;
     a.keep = P.resident; a.src = B.psi; a.dst = B.psi;
     res = axis_pass<T, false, KIND>(P, B, a, S, -1);
     kept = P.resident;
     if (!grid_sync(B, &sflag)) return;
     finish(B, S, 1, D + 1);
-    const double n = S.fin[0];
-    if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
-    for (int b = 0; b < D; ++b) {
-      const double g = S.fin[1 + b] / n;
-      if (!isfinite(g)) { err = ST_NONFINITE; goto done; }
-      if (RN.motion != GRID_FIXED) {
-        const double dpn = sig * g;
-        if (fabs(dpn) > 10.0 * P.N[b] * P.dp[b]) { err = ST_UNSTABLE; goto done; }
-        p[b] -= dpn;
-      }
-    }
-    build_tables(P, B, TB_A, 0.0, delta, p, q, 0.0);
+    centre_after_potential(P, S, RN.motion);
+    if (sc[SC_ERR] != 0.0) goto done;
+    build_tables(P, B, S, TB_A);
     if (!grid_sync(B, &sflag)) return;
+    load_tables(P, B, S, LT_A);
+    __syncthreads();
   }
 
   for (int64_t u = 0; u < RN.n_units; ++u) {
-    double tau, sig;
-    bool hasv;
-    unit_coeffs(RN, gam, u, tau, sig, hasv);
+    if (threadIdx.x == 0) {
+      double tau, sig;
+      bool hasv;
+      unit_coeffs(RN, gam, u, tau, sig, hasv);
+      sc[SC_TAU] = tau;
+      sc[SC_SIG] = sig;
+      sc[SC_SGH] = -sig / P.hbar;
+      sc[SC_HASV] = hasv ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const bool hasv = sc[SC_HASV] != 0.0;
     // forward transform, kinetic moments on the last pass
     for (int i = 0; i < D; ++i) {
       const bool last = (i == D - 1);
@@ -768,22 +893,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (!grid_sync(B, &sflag)) return;
     finish(B, S, 0, D + 1);
-    {
-      const double n = S.fin[0];
-      if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
-      for (int b = 0; b < D; ++b) {
-        const double pi = p[b] + P.dp[b] * (S.fin[1 + b] / n);
-        if (!isfinite(pi)) { err = ST_NONFINITE; goto done; }
-        const double mom = RN.motion == GRID_ADAPTIVE ? pi : p[b];
-        delta[b] = RN.motion == GRID_FIXED ? 0.0 : tau * P.minv[b] * mom;
-        if (fabs(delta[b]) > 10.0 * P.N[b] * P.dq[b]) { err = ST_UNSTABLE; goto done; }
-        qn[b] = q[b] + delta[b];
-      }
-    }
-    build_tables(P, B, TB_K | (hasv ? TB_V : 0), tau, delta, p, qn, -sig / P.hbar);
+    centre_after_kinetic(P, S, RN.motion);
+    if (sc[SC_ERR] != 0.0) goto done;
+    build_tables(P, B, S, TB_K | (hasv ? TB_V : 0));
     if (!grid_sync(B, &sflag)) return;
-#pragma unroll
-    for (int b = 0; b < MAXD; ++b) q[b] = qn[b];
+    load_tables(P, B, S, LT_K | (hasv ? LT_V : 0));
+    if (threadIdx.x < D) sc[SC_Q + threadIdx.x] = sc[SC_QN + threadIdx.x];
+    __syncthreads();
     // inverse transform, potential substep fused into the last pass
     for (int i = 0; i < D; ++i) {
       const bool last = (i == D - 1);
@@ -791,7 +907,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       a.l = i; a.fft = 1; a.pre = PRE_K; a.post = 1;
       a.from_smem = (i == 0 && kept);
       a.keep = last && hasv && P.resident;
-      a.red = (last && hasv) ? RED_V : RED_NONE; a.slot = 1; a.sgh = -sig / P.hbar;
+      a.red = (last && hasv) ? RED_V : RED_NONE; a.slot = 1;
       a.src = B.psi; a.dst = B.psi;
       res = axis_pass<T, true, KIND>(P, B, a, S, res);
       kept = a.keep;
@@ -800,54 +916,55 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (hasv) {
       if (!grid_sync(B, &sflag)) return;
       finish(B, S, 1, D + 1);
-      const double n = S.fin[0];
-      if (!(n > 0) || !isfinite(n)) { err = ST_NONFINITE; goto done; }
-      for (int b = 0; b < D; ++b) {
-        const double g = S.fin[1 + b] / n;
-        if (!isfinite(g)) { err = ST_NONFINITE; goto done; }
-        if (RN.motion != GRID_FIXED) {
-          const double dpn = sig * g;
-          if (fabs(dpn) > 10.0 * P.N[b] * P.dp[b]) { err = ST_UNSTABLE; goto done; }
-          p[b] -= dpn;
-        }
-      }
-      build_tables(P, B, TB_A, 0.0, delta, p, q, 0.0);
+      centre_after_potential(P, S, RN.motion);
+      if (sc[SC_ERR] != 0.0) goto done;
+      build_tables(P, B, S, TB_A);
       if (!grid_sync(B, &sflag)) return;
+      load_tables(P, B, S, LT_A);
+      __syncthreads();
     }
   }
   if (kept) flush_resident<T>(P, B, S, res);
 done:
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int a = 0; a < D; ++a) {
-      B.ctrl[a] = q[a];
-      B.ctrl[8 + a] = p[a];
+      B.ctrl[a] = sc[SC_Q + a];
+      B.ctrl[8 + a] = sc[SC_P + a];
     }
-    if (err != ST_OK) atomicExch(B.status, err);
+    if (sc[SC_ERR] != 0.0) atomicExch(B.status, (int)sc[SC_ERR]);
   }
 }
 
 // Tables A/Ainv for the current p-centre (after a state upload).
 __global__ void __launch_bounds__(THREADS) k_init_tables(const __grid_constant__ Plan P,
                                                           const __grid_constant__ Bufs B) {
-  double p[MAXD], q[MAXD], z[MAXD];
-  for (int a = 0; a < MAXD; ++a) {
-    p[a] = a < P.D ? B.ctrl[8 + a] : 0.0;
-    q[a] = a < P.D ? B.ctrl[a] : 0.0;
-    z[a] = 0.0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<double2> S = carve<double2>(P, smem_raw);
+  if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < P.D) {
+    S.sc[SC_P + threadIdx.x] = B.ctrl[8 + threadIdx.x];
+    S.sc[SC_Q + threadIdx.x] = B.ctrl[threadIdx.x];
   }
-  build_tables(P, B, TB_A, 0.0, z, p, q, 0.0);
+  load_tables(P, B, S, LT_SCT);
+  __syncthreads();
+  build_tables(P, B, S, TB_A);
 }
 
 // Observables: tables of V (unscaled) and of the kinetic energy.
 __global__ void __launch_bounds__(THREADS) k_obs_tables(const __grid_constant__ Plan P,
                                                          const __grid_constant__ Bufs B) {
-  double p[MAXD], q[MAXD], z[MAXD];
-  for (int a = 0; a < MAXD; ++a) {
-    p[a] = a < P.D ? B.ctrl[8 + a] : 0.0;
-    q[a] = a < P.D ? B.ctrl[a] : 0.0;
-    z[a] = 0.0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<double2> S = carve<double2>(P, smem_raw);
+  if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < P.D) {
+    S.sc[SC_P + threadIdx.x] = B.ctrl[8 + threadIdx.x];
+    S.sc[SC_QN + threadIdx.x] = B.ctrl[threadIdx.x];
   }
-  build_tables(P, B, TB_V | TB_E, 0.0, z, p, q, 1.0);
+  if (threadIdx.x == 0) S.sc[SC_SGH] = 1.0;
+  __syncthreads();
+  build_tables(P, B, S, TB_V | TB_E);
 }
 
 // Observables: one forward pass (out of place into scratch) or the V pass.
@@ -857,12 +974,14 @@ __global__ void __launch_bounds__(THREADS)
   using V = typename VT<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem<V> S = carve<V>(P, smem_raw);
-  double q[MAXD];
-  for (int a = 0; a < MAXD; ++a) q[a] = a < P.D ? B.ctrl[a] : 0.0;
+  if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < P.D) S.sc[SC_Q + threadIdx.x] = B.ctrl[threadIdx.x];
+  if (threadIdx.x == 0) S.sc[SC_SGH] = 1.0;
+  load_tables(P, B, S, LT_TW | LT_A | LT_C | LT_V | LT_E | LT_SCT);
+  __syncthreads();
   PassArgs a{};
   a.l = l;
-  a.q = q;
-  a.sgh = 1.0;
   if (mode == 0) {  // forward transform pass; kinetic moments on axis 0
     a.fft = 1; a.pre = PRE_A;
     a.red = (l == 0) ? RED_OBS_KIN : RED_NONE; a.slot = 0;

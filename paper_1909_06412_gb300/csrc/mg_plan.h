@@ -65,6 +65,7 @@ struct Bufs {
   double* tabC;          // k - N_l/2 as double
   double* tabE;          // per-axis kinetic energy minv_l (p_l^K)^2 / 2
   const double* gamma;   // composition coefficients
+  double2* sct;          // 256 entries e^{i k pi / 128}
   double2* scratch;      // npts complex128 (observables, host staging)
 };
 
