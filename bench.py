@@ -39,6 +39,10 @@ STEPS_PER_CALL = 100
 CPU_SAMPLE_STEPS = 30
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
+# DRAM bytes (read + write) of one propagate launch, from an ncu capture of
+# `python bench.py --profile`; valid only for the kernel source it was taken on.
+TRAFFIC_RECORD = {"kernel_sha256": None, "bytes_per_launch": None}
+
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -58,6 +62,14 @@ def initial(mgmod):
     rbar = mgmod.mg_morse_mean(POT[0], POT[1], POT[2], 0.5 * AMU)
     fac = [("gauss", 8.0, -10.0, 0.5), ("morse", POT[0], POT[1], POT[2], 0.5 * AMU)]
     return fac, [8.0, rbar], [-10.0, 0.0]
+
+
+def traffic_per_launch():
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1909_06412_gb300", "csrc", "mg_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return TRAFFIC_RECORD["bytes_per_launch"] if h == TRAFFIC_RECORD["kernel_sha256"] else None
 
 
 def peaks():
@@ -201,8 +213,8 @@ def cpu_baseline_and_error(mgmod, torch):
 
 
 def run_profile(args):
-    """A short run of the same workload for profiler captures: the propagate
-    kernel is launched warmup + steps times, 10 time steps per launch."""
+    """The timed launches of the workload alone, for profiler captures: the
+    propagate kernel is launched warmup + steps times, STEPS_PER_CALL steps each."""
     import torch
     import paper_1909_06412_gb300 as mg
 
@@ -211,7 +223,7 @@ def run_profile(args):
     g.set_potential(mg.MG_POT_ATOM_DIATOM, POT)
     g.set_separable(fac, qc, pc)
     for _ in range(args.warmup + args.steps):
-        g.propagate(10, DT, SCHEME)
+        g.propagate(STEPS_PER_CALL, DT, SCHEME)
     g.sync()
     print(json.dumps({"profile_run": True, "launches": g.launches}))
 
@@ -223,7 +235,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", action="store_true",
-                    help="only warm-up and timed propagate calls of 10 steps (for ncu captures)")
+                    help="only the warm-up and timed propagate calls, as in the timed region (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -324,7 +336,7 @@ def main():
         "error_vs_oracle": err,
         "roofline": {
             "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(),
             "kernel": "k_propagate (persistent, one launch per call)",
             "flops_per_point_stage": flops_ps,
             "peak_source": "FP64 FMA units x clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
