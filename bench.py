@@ -228,6 +228,50 @@ def run_profile(args):
     print(json.dumps({"profile_run": True, "launches": g.launches}))
 
 
+def mixed_precision_leg(mgmod, torch, dev, args, flush):
+    """The same workload with FP32 storage and transforms (FP64 phase
+    arguments, reductions and centres): device throughput timed like the main
+    line, and its error against the FP64 oracle on the CPU-baseline sample."""
+    import oracle
+
+    fac, qc, pc = initial(mgmod)
+    g = mgmod.Propagator(N_GRID, DQ, minv=MINV, device=dev, precision=mgmod.MG_FP32_MIXED)
+    g.set_potential(mgmod.MG_POT_ATOM_DIATOM, POT)
+    g.set_separable(fac, qc, pc)
+    for _ in range(max(3, args.warmup)):
+        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+    g.sync()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+        e1.record(g.stream)
+        ms.append((e0, e1))
+    g.sync()
+    t = sum(a.elapsed_time(b) for a, b in ms) / 1e3
+    npts = int(np.prod(N_GRID))
+    g2 = mgmod.Propagator(N_GRID, DQ, minv=MINV, device=dev, precision=mgmod.MG_FP32_MIXED)
+    g2.set_potential(mgmod.MG_POT_ATOM_DIATOM, POT)
+    g2.set_separable(fac, qc, pc)
+    g2.propagate(CPU_SAMPLE_STEPS, DT, SCHEME)
+    psi, q, p, _ = g2.get_state()
+    o = oracle.Grid(N_GRID, DQ, minv=MINV)
+    o.set_potential(oracle.POT_ATOM_DIATOM, POT)
+    o.set_separable(fac, qc, pc)
+    o.propagate(CPU_SAMPLE_STEPS, DT, SCHEME)
+    psi_o, q_o, p_o, _ = o.get_state()
+    return {
+        "dtype": "f32 storage/transforms, f64 phase arguments, reductions and centres",
+        "value": npts * STEPS_PER_CALL * args.steps / t, "unit": UNIT,
+        "ms_per_step": 1e3 * t / args.steps,
+        "error_vs_oracle": {"psi_rel_l2": float(np.linalg.norm(psi - psi_o) / np.linalg.norm(psi_o)),
+                            "q_abs": float(np.abs(q - q_o).max()), "p_abs": float(np.abs(p - p_o).max()),
+                            "steps": CPU_SAMPLE_STEPS},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,6 +364,7 @@ def main():
     achieved_tf = flops_ps * npts * stages_per_call / t_launch / 1e12
     achieved_gbs = algorithmic_bytes_per_point_stage() * npts * stages_per_call / t_launch / 1e9
     cpu, err = cpu_baseline_and_error(mg, torch)
+    mixed = mixed_precision_leg(mg, torch, dev, args, flush)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -344,6 +389,7 @@ def main():
                     "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
                     "bytes_per_point_stage": algorithmic_bytes_per_point_stage()},
         },
+        "mixed_precision": mixed,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,

@@ -167,6 +167,26 @@ bool scheme_coeffs(const char* name, std::vector<double>& g) {
   return (int)g.size() <= MAX_STAGES;
 }
 
+// Host twin of the kernels' round_unit_f32: the float pair bracketing (x, y)
+// whose squared modulus is closest to 1 (FP32 twiddles without a norm bias).
+void round_unit_f32_host(double x, double y, double* ox, double* oy) {
+  const float xf = (float)x, yf = (float)y;
+  const float xs[2] = {xf, (double)xf < x ? std::nextafterf(xf, INFINITY) : std::nextafterf(xf, -INFINITY)};
+  const float ys[2] = {yf, (double)yf < y ? std::nextafterf(yf, INFINITY) : std::nextafterf(yf, -INFINITY)};
+  double best = INFINITY;
+  *ox = xf;
+  *oy = yf;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const double e = std::fabs((double)xs[a] * xs[a] + (double)ys[b] * ys[b] - 1.0);
+      if (e < best) {
+        best = e;
+        *ox = xs[a];
+        *oy = ys[b];
+      }
+    }
+}
+
 // e^{i k pi/128}, k = 0..255, for the table-driven sincos of the kernels.
 void fill_sincos_table(double* t) {
   for (int k = 0; k < 256; ++k) {
@@ -285,7 +305,6 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
   *out = nullptr;
   if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar)) return MG_ERR_ARG;
   if (precision != MG_FP64 && precision != MG_FP32_MIXED) return MG_ERR_ARG;
-  if (precision != MG_FP64) return MG_ERR_UNSUPPORTED;
   for (int l = 0; l < D; ++l) {
     if (N[l] < 2 || N[l] % 2) return MG_ERR_ARG;
     if (!(dq[l] > 0) || !std::isfinite(dq[l])) return MG_ERR_ARG;
@@ -385,6 +404,9 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
       const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
       tw[2 * (P.ax[l].toff + m)] = (double)std::cos(ang);
       tw[2 * (P.ax[l].toff + m) + 1] = -(double)std::sin(ang);
+      if (P.prec)
+        round_unit_f32_host(tw[2 * (P.ax[l].toff + m)], tw[2 * (P.ax[l].toff + m) + 1],
+                            &tw[2 * (P.ax[l].toff + m)], &tw[2 * (P.ax[l].toff + m) + 1]);
       kc[P.ax[l].toff + m] = (double)(m - n / 2);
     }
   }

@@ -472,6 +472,45 @@ __device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, d
 
 enum { TB_K = 1, TB_V = 2, TB_A = 4, TB_E = 8 };
 
+// e^{i theta} for a table entry: FP64 for FP64 storage; for FP32 storage the
+// FP64 argument is reduced modulo 2 pi in FP64 and the sine and cosine are
+// taken in FP32 (the entry is rounded to FP32 anyway).
+__device__ __forceinline__ void expi_prec(int prec, double th, const double2* tab, double& s, double& c) {
+  if (!prec) {
+    expi_tab(th, tab, s, c);
+    return;
+  }
+  const double kk = rint(th * 0.15915494309189535);
+  double r = fma(-kk, 6.283185307179586, th);
+  r = fma(-kk, 2.4492935982947064e-16, r);
+  float sf, cf;
+  sincosf((float)r, &sf, &cf);
+  s = sf;
+  c = cf;
+}
+
+// For FP32 storage: of the four float pairs that bracket (x, y), the one whose
+// squared modulus is closest to m2.  Plain rounding leaves |w|^2 - 1 at ~1e-7
+// with a fixed sign per entry, a bias that a table reused by every transform
+// turns into a steady norm drift; this choice keeps each multiplier unitary to
+// ~1e-9 while staying within one float ulp of the exact value.
+__device__ double2 round_unit_f32(double x, double y, double m2) {
+  const float xf = (float)x, yf = (float)y;
+  const float xs[2] = {xf, (double)xf < x ? nextafterf(xf, INFINITY) : nextafterf(xf, -INFINITY)};
+  const float ys[2] = {yf, (double)yf < y ? nextafterf(yf, INFINITY) : nextafterf(yf, -INFINITY)};
+  double best = INFINITY;
+  double2 r = make_double2(xf, yf);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const double e = fabs(fma((double)xs[a], (double)xs[a], (double)ys[b] * (double)ys[b]) - m2);
+      if (e < best) {
+        best = e;
+        r = make_double2(xs[a], ys[b]);
+      }
+    }
+  return r;
+}
+
 // Distributed construction of the per-axis tables.  The work is cut into
 // tasks of 32 consecutive entries of one table, one task per warp with every
 // lane busy (an FP64 warp instruction costs the same with 1 or 32 lanes), and
@@ -503,16 +542,22 @@ template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B,
       const double pk = fma(c, P.dp[a], sc[SC_P + a]);
       const double th = (sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk) / P.hbar;
       double sn, cs;
-      expi_tab(th, S.sct, sn, cs);
-      __stcg(B.tabK + e, make_double2(cs, sn));
+      expi_prec(P.prec, th, S.sct, sn, cs);
+      __stcg(B.tabK + e, P.prec ? round_unit_f32(cs, sn, 1.0) : make_double2(cs, sn));
     } else if (kind == TB_A) {
       const double th = -sc[SC_P + a] * c * P.dq[a] / P.hbar;
       double sn, cs;
-      expi_tab(th, S.sct, sn, cs);
+      expi_prec(P.prec, th, S.sct, sn, cs);
       const double sg = (j & 1) ? -1.0 : 1.0;
-      __stcg(B.tabA + e, make_double2(sg * cs, sg * sn));
       // conj(A)/N by division: a rounded 1/N would bias every inverse transform
-      __stcg(B.tabAi + e, make_double2(sg * cs / (double)n, -sg * sn / (double)n));
+      if (P.prec) {
+        __stcg(B.tabA + e, round_unit_f32(sg * cs, sg * sn, 1.0));
+        const double inv = 1.0 / ((double)n * (double)n);
+        __stcg(B.tabAi + e, round_unit_f32(sg * cs / (double)n, -sg * sn / (double)n, inv));
+      } else {
+        __stcg(B.tabA + e, make_double2(sg * cs, sg * sn));
+        __stcg(B.tabAi + e, make_double2(sg * cs / (double)n, -sg * sn / (double)n));
+      }
     } else if (kind == TB_V) {
       vcolumns(P, B, e, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH]);
     } else {
@@ -584,6 +629,14 @@ struct PassArgs {
   void* dst;
 };
 
+// s + c += x with Knuth's error-free two-sum (FP32).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
 // Multi-index of element j of line (o, i) of axis l.
 __device__ __forceinline__ void decode(const Plan& P, int l, unsigned o, unsigned i, int j, int* idx) {
   for (int a = l - 1; a >= 0; --a) {
@@ -618,6 +671,12 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   double acc[MAXD + 2];
 #pragma unroll
   for (int v = 0; v < MAXD + 2; ++v) acc[v] = 0;
+  // FP32 storage: the kinetic moments are summed per thread in FP32 with an
+  // error-free two-sum (sum + compensation), so the per-thread partials are
+  // accurate to ~1e-14 without an FP64 instruction per point.
+  float ks[MAXD + 1], kc[MAXD + 1];
+#pragma unroll
+  for (int v = 0; v < MAXD + 1; ++v) ks[v] = kc[v] = 0.f;
 
   const int64_t bid = blockIdx.x, nb = gridDim.x;
   const int64_t mine = bid < ax.ntiles ? (ax.ntiles - bid + nb - 1) / nb : 0;
@@ -632,17 +691,33 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
     if (A.from_smem) {
       cur = S.reg[res_in];
     } else {
+      // up to LOADS independent global loads in flight per thread before the
+      // shared-memory stores (one L2 round trip instead of one per element)
+      constexpr int LOADS = 4;
       cur = S.reg[0];
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int ti = e / (W * n);
-        const int rem = e - ti * W * n;
-        int w, j;
-        if (contig) { w = rem / n; j = rem - w * n; }
-        else { j = rem / W; w = rem - j * W; }
-        const int64_t t = bid + (c0 + ti) * nb;
-        const int64_t o = t / tpo;
-        const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
-        cur[(ti * W + w) * n + j] = __ldcg(src + base + j * es + w * ws);
+      for (int e0 = threadIdx.x; e0 < cnt; e0 += LOADS * blockDim.x) {
+        V vals[LOADS];
+        int dsti[LOADS];
+#pragma unroll
+        for (int u = 0; u < LOADS; ++u) {
+          const int e = e0 + u * blockDim.x;
+          dsti[u] = -1;
+          if (e < cnt) {
+            const int ti = e / (W * n);
+            const int rem = e - ti * W * n;
+            int w, j;
+            if (contig) { w = rem / n; j = rem - w * n; }
+            else { j = rem / W; w = rem - j * W; }
+            const int64_t t = bid + (c0 + ti) * nb;
+            const int64_t o = t / tpo;
+            const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
+            vals[u] = __ldcg(src + base + j * es + w * ws);
+            dsti[u] = (ti * W + w) * n + j;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < LOADS; ++u)
+          if (dsti[u] >= 0) cur[dsti[u]] = vals[u];
       }
     }
     __syncthreads();
@@ -670,8 +745,22 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
         const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
         const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
         decode(P, A.l, lo, li, j, idx);
-        const double2 d = to_d2(v);
-        const double w2 = fma(d.x, d.x, d.y * d.y);
+        // |value|^2: FP64 for FP64 storage; FP32 product, FP64 accumulation otherwise
+        bool handled = false;
+        if constexpr (sizeof(T) == 4) {
+          if (A.red == RED_KIN) {
+            const float w2f = fmaf(v.x, v.x, v.y * v.y);
+            two_sum_acc(ks[0], kc[0], w2f);
+#pragma unroll
+            for (int a = 0; a < MAXD; ++a)
+              if (a < D) two_sum_acc(ks[1 + a], kc[1 + a], (float)(idx[a] - (P.ax[a].n >> 1)) * w2f);
+            handled = true;
+          }
+        }
+        if (!handled) {
+        double w2;
+        if constexpr (sizeof(T) == 8) w2 = fma((double)v.x, (double)v.x, (double)v.y * (double)v.y);
+        else w2 = (double)fmaf(v.x, v.x, v.y * v.y);
         acc[0] += w2;
         if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
           double te = 0;
@@ -689,15 +778,27 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
 #pragma unroll
             for (int a = 0; a < MAXD; ++a)
               if (a < D) acc[1 + a] = fma(g[a], w2, acc[1 + a]);
-            double sn, cs;
-            expi_tab(th, S.sct, sn, cs);
-            v = from_d2<V>(make_double2(fma(d.x, cs, -d.y * sn), fma(d.x, sn, d.y * cs)));
+            if constexpr (sizeof(T) == 8) {
+              double sn, cs;
+              expi_tab(th, S.sct, sn, cs);
+              v = V{fma(v.x, cs, -v.y * sn), fma(v.x, sn, v.y * cs)};
+            } else {
+              // FP64 phase argument reduced modulo 2 pi (two-word 2 pi), then
+              // FP32 sine and cosine of the reduced angle (|r| <= pi)
+              const double kk = rint(th * 0.15915494309189535);
+              double r = fma(-kk, 6.283185307179586, th);
+              r = fma(-kk, 2.4492935982947064e-16, r);
+              float sn, cs;
+              sincosf((float)r, &sn, &cs);
+              v = V{fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs)};
+            }
           } else {  // observables: <x> and <V>
 #pragma unroll
             for (int a = 0; a < MAXD; ++a)
               if (a < D) acc[1 + a] = fma(fma(S.tc[P.ax[a].toff + idx[a]], P.dq[a], S.sc[SC_Q + a]), w2, acc[1 + a]);
             acc[D + 1] = fma(th, w2, acc[D + 1]);
           }
+        }
         }
       }
       if (A.keep) cur[si] = v;
@@ -710,6 +811,12 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
     res = cur == S.reg[0] ? 0 : 1;
   }
   if (A.red != RED_NONE) {
+    if constexpr (sizeof(T) == 4) {
+      if (A.red == RED_KIN) {
+#pragma unroll
+        for (int v = 0; v < MAXD + 1; ++v) acc[v] = (double)ks[v] + (double)kc[v];
+      }
+    }
     const int nv = (A.red == RED_OBS_KIN || A.red == RED_OBS_V) ? D + 2 : D + 1;
     block_partials(B, S, A.slot, acc, nv);
   }
@@ -1001,24 +1108,32 @@ __global__ void __launch_bounds__(THREADS)
 template <typename T, int KIND> static void* prop_fn() { return (void*)k_propagate<T, KIND>; }
 template <typename T, int KIND> static void* obs_fn() { return (void*)k_obs_pass<T, KIND>; }
 
+// prec 0: FP64 storage and arithmetic; prec 1: FP32 storage and transforms
+// with FP64 phase arguments, reductions and grid centres.
 void* propagate_kernel(int prec, int kind) {
-  if (prec != 0) return nullptr;
-  switch (kind) {
-    case POT_HARMONIC: return prop_fn<double, POT_HARMONIC>();
-    case POT_ATOM_DIATOM: return prop_fn<double, POT_ATOM_DIATOM>();
-    case POT_HENON_HEILES: return prop_fn<double, POT_HENON_HEILES>();
-    case POT_SECREST_JOHNSON: return prop_fn<double, POT_SECREST_JOHNSON>();
+  switch (kind * 2 + prec) {
+    case POT_HARMONIC * 2: return prop_fn<double, POT_HARMONIC>();
+    case POT_ATOM_DIATOM * 2: return prop_fn<double, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES * 2: return prop_fn<double, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON * 2: return prop_fn<double, POT_SECREST_JOHNSON>();
+    case POT_HARMONIC * 2 + 1: return prop_fn<float, POT_HARMONIC>();
+    case POT_ATOM_DIATOM * 2 + 1: return prop_fn<float, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES * 2 + 1: return prop_fn<float, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON * 2 + 1: return prop_fn<float, POT_SECREST_JOHNSON>();
   }
   return nullptr;
 }
 
 void* obs_kernel(int prec, int kind) {
-  if (prec != 0) return nullptr;
-  switch (kind) {
-    case POT_HARMONIC: return obs_fn<double, POT_HARMONIC>();
-    case POT_ATOM_DIATOM: return obs_fn<double, POT_ATOM_DIATOM>();
-    case POT_HENON_HEILES: return obs_fn<double, POT_HENON_HEILES>();
-    case POT_SECREST_JOHNSON: return obs_fn<double, POT_SECREST_JOHNSON>();
+  switch (kind * 2 + prec) {
+    case POT_HARMONIC * 2: return obs_fn<double, POT_HARMONIC>();
+    case POT_ATOM_DIATOM * 2: return obs_fn<double, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES * 2: return obs_fn<double, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON * 2: return obs_fn<double, POT_SECREST_JOHNSON>();
+    case POT_HARMONIC * 2 + 1: return obs_fn<float, POT_HARMONIC>();
+    case POT_ATOM_DIATOM * 2 + 1: return obs_fn<float, POT_ATOM_DIATOM>();
+    case POT_HENON_HEILES * 2 + 1: return obs_fn<float, POT_HENON_HEILES>();
+    case POT_SECREST_JOHNSON * 2 + 1: return obs_fn<float, POT_SECREST_JOHNSON>();
   }
   return nullptr;
 }
