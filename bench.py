@@ -228,6 +228,55 @@ def run_profile(args):
     print(json.dumps({"profile_run": True, "launches": g.launches}))
 
 
+def other_workloads(mgmod, torch, dev, flush):
+    """The paper's other workload shapes, each timed over one propagate call
+    after one warm-up call (state resident in HBM, L2 flushed before the call):
+    3D harmonic 32^3 FP64 Strang; 8D Henon-Heiles 12^8 FP64 and 16^8 FP32,
+    fourth-order Suzuki, dt = 0.01."""
+    out = []
+    cases = [
+        ("3D harmonic 32^3 FP64, strang, dt=0.01", (32, 32, 32), (0.3,) * 3, mgmod.MG_FP64,
+         mgmod.MG_POT_HARMONIC, list(np.diag(np.array([1.0, 1.2, 1.5]) ** 2).ravel()) + [0.0] * 3,
+         [("gauss", q, p, w ** -0.5) for q, p, w in zip((1.0, -0.5, 0.8), (0.0, 0.5, -0.3), (1.0, 1.2, 1.5))],
+         (1.0, -0.5, 0.8), (0.0, 0.5, -0.3), "strang", 1, 0.01, 200, 16),
+        ("8D Henon-Heiles 12^8 FP64, suzuki4, dt=0.01", (12,) * 8, (math.sqrt(2 * math.pi / 12),) * 8,
+         mgmod.MG_FP64, mgmod.MG_POT_HENON_HEILES, [0.111803], [("gauss", 2.0, 0.0, 1.0)] * 8,
+         (2.0,) * 8, (0.0,) * 8, "suzuki4", 5, 0.01, 2, 16),
+        ("8D Henon-Heiles 16^8 FP32 mixed, suzuki4, dt=0.01", (16,) * 8, (math.sqrt(2 * math.pi / 16),) * 8,
+         mgmod.MG_FP32_MIXED, mgmod.MG_POT_HENON_HEILES, [0.111803], [("gauss", 2.0, 0.0, 1.0)] * 8,
+         (2.0,) * 8, (0.0,) * 8, "suzuki4", 5, 0.01, 2, 8),
+    ]
+    for name, N, dq, prec, kind, pot, fac, q0, p0, scheme, stages, dt, steps, elem in cases:
+        g = mgmod.Propagator(N, dq, precision=prec, device=dev)
+        g.set_potential(kind, pot)
+        g.set_separable(fac, q0, p0)
+        n0 = g.observables()[0]
+        g.propagate(1, dt, scheme)
+        g.sync()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        g.propagate(steps, dt, scheme)
+        e1.record(g.stream)
+        g.sync()
+        t = e0.elapsed_time(e1) / 1e3
+        n1 = g.observables()[0]
+        npts = int(np.prod(N))
+        ps = npts * steps * stages / t
+        D = len(N)
+        out.append({
+            "workload": name, "value": npts * steps / t, "unit": UNIT, "points": npts,
+            "stages_per_step": stages, "ms_per_step": 1e3 * t / steps,
+            "hbm_gbs_algorithmic": ps * 4 * elem / 1e9,
+            "fp64_tflops_algorithmic": ps * algorithmic_flops_per_point_stage(N, D) / 1e12 if prec == 0 else None,
+            "norm_drift": n1 / n0 - 1,
+        })
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def mixed_precision_leg(mgmod, torch, dev, args, flush):
     """The same workload with FP32 storage and transforms (FP64 phase
     arguments, reductions and centres): device throughput timed like the main
@@ -365,6 +414,7 @@ def main():
     achieved_gbs = algorithmic_bytes_per_point_stage() * npts * stages_per_call / t_launch / 1e9
     cpu, err = cpu_baseline_and_error(mg, torch)
     mixed = mixed_precision_leg(mg, torch, dev, args, flush)
+    others = other_workloads(mg, torch, dev, flush)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -390,6 +440,7 @@ def main():
                     "bytes_per_point_stage": algorithmic_bytes_per_point_stage()},
         },
         "mixed_precision": mixed,
+        "other_workloads": others,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,

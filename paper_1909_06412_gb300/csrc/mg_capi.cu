@@ -17,6 +17,7 @@ void* propagate_kernel(int prec, int kind);
 void* obs_kernel(int prec, int kind);
 void* init_tables_kernel();
 void* obs_tables_kernel();
+void* set_product_kernel(int prec);
 }  // namespace mgk
 
 using namespace mgk;
@@ -33,7 +34,7 @@ struct Layout {
   size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, scratch, total;
 };
 
-Layout layout_for(int D, const int64_t* N) {
+Layout layout_for(int D, const int64_t* N, int precision) {
   int64_t npts = 1, tt = 0;
   for (int l = 0; l < D; ++l) {
     npts *= N[l];
@@ -59,7 +60,7 @@ Layout layout_for(int D, const int64_t* N) {
   L.tabE = put(tt * sizeof(double));
   L.gamma = put(MAX_STAGES * sizeof(double));
   L.sct = put(256 * sizeof(double2));
-  L.scratch = put((size_t)npts * sizeof(double2));
+  L.scratch = put((size_t)npts * (precision == 0 ? sizeof(double2) : sizeof(float2)));
   L.total = o;
   return L;
 }
@@ -97,11 +98,43 @@ size_t smem_for(const Plan& P) {
   const size_t TT = (size_t)P.tab_total;
   size_t s = 4 * r16(vs * TT) + r16(sizeof(double) * NVCOL * TT) + 2 * r16(sizeof(double) * TT) +
              r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (P.D + 2)) +
-             r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * 40) + 2 * r16((size_t)P.region_bytes);
+             r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * 40) +
+             (P.resident ? 2 : 3) * r16((size_t)P.region_bytes) + r16(sizeof(uint64_t) * 3) +
+             r16(sizeof(unsigned) * 4) + r16(sizeof(int64_t) * P.max_tiles) +
+             r16(sizeof(uint16_t) * P.max_lines * P.D);
   return s;
 }
 
 // Tile and chunk sizes for a given grid size of the persistent kernel.
+constexpr int64_t SMEM_CAP = 227 * 1024;  // dynamic shared memory a CTA may use
+
+void chunk_plan(Plan& P, int64_t region) {
+  const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
+  const int D = P.D;
+  P.region_bytes = (int)((region + 15) & ~int64_t(15));
+  for (int l = 0; l < D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    const int64_t tile_bytes = (int64_t)ax.W * ax.n * vs;
+    ax.tpc = (int)std::max<int64_t>(1, P.region_bytes / tile_bytes);
+    // butterflies a CTA has per pass; aim for at least one warp per sub-partition
+    const int64_t mine = (ax.ntiles + P.nblocks - 1) / P.nblocks;
+    const int64_t lines = std::min<int64_t>(mine, ax.tpc) * ax.W;
+    const int rmax = lines * ax.n / 8 >= 128 ? 8 : (lines * ax.n / 4 >= 128 ? 4 : 2);
+    radix_plan(ax.n, ax, rmax);
+  }
+  // per-chunk tile offsets and line indices live in shared memory
+  P.max_tiles = 1;
+  P.max_lines = 1;
+  for (int l = 0; l < D; ++l) {
+    const AxisPlan& ax = P.ax[l];
+    const int64_t mine = std::max<int64_t>((ax.ntiles + P.nblocks - 1) / P.nblocks, 1);
+    const int64_t tiles = (P.resident && (l == 0 || l == D - 1)) ? mine : std::min<int64_t>(ax.tpc, mine);
+    P.max_tiles = (int)std::max<int64_t>(P.max_tiles, tiles);
+    P.max_lines = (int)std::max<int64_t>(P.max_lines, tiles * ax.W);
+  }
+  P.smem_bytes = (int)smem_for(P);
+}
+
 void tile_plan(Plan& P) {
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const int D = P.D;
@@ -121,19 +154,33 @@ void tile_plan(Plan& P) {
     }
   }
   P.resident = need_res <= RESIDENT_CAP;
-  int64_t region = P.resident ? std::max(need_res, need_min) : std::max<int64_t>(CHUNK_REGION, need_min);
-  P.region_bytes = (int)((region + 15) & ~int64_t(15));
-  for (int l = 0; l < D; ++l) {
-    AxisPlan& ax = P.ax[l];
-    const int64_t tile_bytes = (int64_t)ax.W * ax.n * vs;
-    ax.tpc = (int)std::max<int64_t>(1, P.region_bytes / tile_bytes);
-    // butterflies a CTA has per pass; aim for at least one warp per sub-partition
-    const int64_t mine = (ax.ntiles + P.nblocks - 1) / P.nblocks;
-    const int64_t lines = std::min<int64_t>(mine, ax.tpc) * ax.W;
-    const int rmax = lines * ax.n / 8 >= 128 ? 8 : (lines * ax.n / 4 >= 128 ? 4 : 2);
-    radix_plan(ax.n, ax, rmax);
+  if (P.resident) {
+    chunk_plan(P, std::max(need_res, need_min));
+    return;
   }
-  P.smem_bytes = (int)smem_for(P);
+  // HBM-streamed passes: three chunk regions (load, transform, prefetch).  A
+  // tile is as large as a region allows, so that the TMA engine moves it in a
+  // few large copies: on the contiguous axis W consecutive lines (one copy), on
+  // a strided axis n rows of W adjacent elements (one copy per row).
+  int64_t region = CHUNK_REGION;
+  for (;;) {
+    for (int l = 0; l < D; ++l) {
+      AxisPlan& ax = P.ax[l];
+      const int64_t lim = std::max<int64_t>(1, region / ((int64_t)ax.n * vs));
+      const int64_t lines = P.npts / ax.n;
+      const int64_t mult = (l == D - 1) ? lines : ax.stride;  // W must divide this
+      int64_t W = 1;
+      while (W * 2 <= lim && mult % (W * 2) == 0) W *= 2;
+      if (l < D - 1 && W * vs < 16) W = std::min<int64_t>(ax.stride, 16 / (int64_t)vs);  // 16-byte rows
+      ax.W = (int)W;
+      ax.ntiles = lines / W;
+    }
+    need_min = 0;
+    for (int l = 0; l < D; ++l) need_min = std::max<int64_t>(need_min, (int64_t)P.ax[l].W * P.ax[l].n * vs);
+    chunk_plan(P, std::max(region, need_min));
+    if (P.smem_bytes <= SMEM_CAP || region <= 4096) break;
+    region = region - region / 8 - 16;
+  }
 }
 
 // ---- composition coefficients (eq:comp_TVT; Yoshida 1990 triple jump,
@@ -296,7 +343,7 @@ size_t mg_workspace_bytes(int D, const int64_t* N, int precision) {
   if (D < 1 || D > MAXD || !N || (precision != MG_FP64 && precision != MG_FP32_MIXED)) return 0;
   for (int l = 0; l < D; ++l)
     if (!axis_supported(N[l])) return 0;
-  return layout_for(D, N).total;
+  return layout_for(D, N, precision).total;
 }
 
 mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv, double hbar,
@@ -318,7 +365,7 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
       if (a == b && !(v > 0)) return MG_ERR_ARG;
     }
   if (((uintptr_t)d_work & 255) || ((uintptr_t)d_psi & 15)) return MG_ERR_ARG;
-  Layout L = layout_for(D, N);
+  Layout L = layout_for(D, N, precision);
   if (work_bytes < L.total) return MG_ERR_ARG;
 
   mg_ctx* c = new mg_ctx();
@@ -536,26 +583,24 @@ mg_status mg_set_separable(mg_ctx* c, const int* kinds, const double* params, co
       fac[l][2 * j + 1] = im;
     }
   }
-  const size_t n = (size_t)P.npts;
+  // The outer product is formed on the device from the per-axis factors
+  // (first axis scaled by sqrt(prod dq)), staged in the kinetic table, which
+  // every propagation rebuilds before use.
   const double sc = sqrt_cell(P);
-  mg_status s = cuda_ok(cudaStreamSynchronize(c->stream));
-  if (s != MG_OK) return s;
-  c->host.resize(2 * n);
-  for (size_t J = 0; J < n; ++J) {
-    size_t rem = J;
-    double re = sc, im = 0.0;
-    for (int l = D - 1; l >= 0; --l) {
-      const size_t j = rem % (size_t)P.N[l];
-      rem /= (size_t)P.N[l];
-      const double fr = fac[l][2 * j], fi = fac[l][2 * j + 1];
-      const double nr = re * fr - im * fi;
-      im = re * fi + im * fr;
-      re = nr;
+  std::vector<double> f(2 * (size_t)P.tab_total);
+  for (int l = 0; l < D; ++l)
+    for (int j = 0; j < (int)P.N[l]; ++j) {
+      const double m = l == 0 ? sc : 1.0;
+      f[2 * (P.ax[l].toff + j)] = fac[l][2 * j] * m;
+      f[2 * (P.ax[l].toff + j) + 1] = fac[l][2 * j + 1] * m;
     }
-    c->host[2 * J] = re;
-    c->host[2 * J + 1] = im;
+  mg_status s = cuda_ok(cudaStreamSynchronize(c->stream));
+  if (s == MG_OK)
+    s = cuda_ok(cudaMemcpyAsync(c->B.tabK, f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) {
+    void* args[] = {&c->P, &c->B};
+    s = launch_plain(c, set_product_kernel(P.prec), args, 0);
   }
-  s = upload_u(c);
   if (s != MG_OK) return s;
   for (int a = 0; a < D; ++a) {
     c->q[a] = q_ctr[a];

@@ -142,24 +142,51 @@ template <bool INV, typename V> struct Dft<INV, 8, V> {
 // Stockham FFT in shared memory
 // ---------------------------------------------------------------------------
 
+// Exact quotient x / d for 0 <= x < 2^16 and 1 <= d < 2^16 from m = ceil(2^32/d):
+// floor(x m / 2^32) = floor(x/d + x e) with 0 <= x e < 2^-16 < 1/d, so the
+// result never crosses the next integer.  Replaces runtime integer division
+// in the index arithmetic of the passes.
+struct Div16 {
+  unsigned m;  // 0 encodes d = 1 (2^32 does not fit)
+  __device__ __forceinline__ explicit Div16(unsigned d) : m(d > 1 ? 0xFFFFFFFFu / d + 1u : 0u) {}
+  __device__ __forceinline__ unsigned operator()(unsigned x) const { return m ? __umulhi(x, m) : x; }
+};
+
 // One Stockham autosort pass of radix R over L lines of length n (in -> out).
 // The first pass (Ns == 1) has no twiddles; it applies the diagonal
 // pre-multiplier `pre` (A_l or K_l) to its inputs instead, if given.
+// Tile layout: with wsh = 0 a line is n contiguous elements; with wsh > 0 the
+// lines come in tiles of W = 2^wsh lines stored point-major (element p of line
+// w of a tile at p*W + w), so a warp works on adjacent lines and adjacent
+// shared-memory words.
 template <bool INV, int R, typename V>
 __device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __restrict__ out, int n, int L,
-                                              int Ns, const V* __restrict__ tw, const V* __restrict__ pre) {
+                                              int Ns, const V* __restrict__ tw, const V* __restrict__ pre,
+                                              int wsh) {
   const int nR = n / R;
   const int total = L * nR;
   const int ts = n / (Ns * R);
+  const int W = 1 << wsh;
+  const Div16 divL((unsigned)L), divnR((unsigned)nR), divNs((unsigned)Ns);
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int line = b / nR;
-    const int j = b - line * nR;
-    const V* src = in + line * n;
-    V* dst = out + line * n;
+    int line, j, lbase, ps;
+    if (wsh) {
+      j = (int)divL((unsigned)b);
+      line = b - j * L;
+      lbase = (line >> wsh) * W * n + (line & (W - 1));
+      ps = W;
+    } else {
+      line = (int)divnR((unsigned)b);
+      j = b - line * nR;
+      lbase = line * n;
+      ps = 1;
+    }
+    const V* src = in + lbase;
+    V* dst = out + lbase;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[j + r * nR];
-    const int k = j % Ns;
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nR) * ps];
+    const int k = j - (int)divNs((unsigned)j) * Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -173,21 +200,21 @@ __device__ __forceinline__ void stockham_pass(const V* __restrict__ in, V* __res
     Dft<INV, R, V>::run(v);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ps] = v[r];
   }
 }
 
 // Full 1D transform of L lines; returns the buffer that holds the result.
 template <bool INV, typename V>
-__device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw, const V* pre) {
+__device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw, const V* pre, int wsh) {
   int Ns = 1;
   for (int pi = 0; pi < ax.nrad; ++pi) {
     const int R = ax.rad[pi];
     const V* pm = pi == 0 ? pre : nullptr;
-    if (R == 8) stockham_pass<INV, 8>(in, out, ax.n, L, Ns, tw, pm);
-    else if (R == 4) stockham_pass<INV, 4>(in, out, ax.n, L, Ns, tw, pm);
-    else if (R == 3) stockham_pass<INV, 3>(in, out, ax.n, L, Ns, tw, pm);
-    else stockham_pass<INV, 2>(in, out, ax.n, L, Ns, tw, pm);
+    if (R == 8) stockham_pass<INV, 8>(in, out, ax.n, L, Ns, tw, pm, wsh);
+    else if (R == 4) stockham_pass<INV, 4>(in, out, ax.n, L, Ns, tw, pm, wsh);
+    else if (R == 3) stockham_pass<INV, 3>(in, out, ax.n, L, Ns, tw, pm, wsh);
+    else stockham_pass<INV, 2>(in, out, ax.n, L, Ns, tw, pm, wsh);
     __syncthreads();
     V* t = in;
     in = out;
@@ -195,6 +222,39 @@ __device__ V* stockham(V* in, V* out, int L, const AxisPlan& ax, const V* tw, co
     Ns *= R;
   }
   return in;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine) into shared memory with an mbarrier
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// global -> shared bulk copy; 16-byte aligned addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -296,7 +356,11 @@ template <typename V> struct Smem {
   double* red;  // THREADS * (D+2) per-thread partials
   double* fin;  // PSTRIDE finished sums
   double* sc;   // SC_N scalars
-  V* reg[2];    // data regions
+  V* reg[3];    // data regions (the third only for HBM-streamed passes)
+  uint64_t* mbar; // one mbarrier per data region
+  unsigned* mphase; // their phase bits, carried from one streamed pass to the next
+  int64_t* tb;  // element offset of each tile of the current chunk
+  uint16_t* li; // multi-index of each line of the current chunk (D per line)
 };
 
 template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* base) {
@@ -321,6 +385,11 @@ template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* bas
   s.sc = (double*)take(sizeof(double) * SC_N);
   s.reg[0] = (V*)take(P.region_bytes);
   s.reg[1] = (V*)take(P.region_bytes);
+  s.reg[2] = P.resident ? nullptr : (V*)take(P.region_bytes);
+  s.mbar = (uint64_t*)take(sizeof(uint64_t) * 3);
+  s.mphase = (unsigned*)take(sizeof(unsigned) * 4);
+  s.tb = (int64_t*)take(sizeof(int64_t) * P.max_tiles);
+  s.li = (uint16_t*)take(sizeof(uint16_t) * P.max_lines * P.D);
   return s;
 }
 
@@ -652,6 +721,47 @@ __device__ __forceinline__ void decode(const Plan& P, int l, unsigned o, unsigne
   idx[l] = j;
 }
 
+// Queue the bulk copies of chunk (tiles c0 .. c0+nt-1 of this CTA) into region
+// `reg`, completing on `bar`.  Called by warp 0 only.  A strided tile is n
+// rows of W contiguous elements (one copy per row); a contiguous-axis tile is
+// one line of n elements (one copy).
+template <typename V>
+__device__ void issue_chunk(const AxisPlan& ax, bool contig, const V* src, int64_t c0, int nt, V* reg,
+                            uint64_t* bar) {
+  const int lane = threadIdx.x & 31;
+  const int n = ax.n, W = ax.W;
+  const int64_t s = ax.stride, tpo = contig ? 1 : ax.stride / W;
+  const int64_t bid = blockIdx.x, nb = gridDim.x;
+  const unsigned rowbytes = (unsigned)((contig ? W * n : W) * sizeof(V));
+  const int rows = contig ? nt : nt * n;
+  fence_proxy_async();  // earlier generic accesses to `reg` before the async writes
+  if (lane == 0) mbar_expect_tx(bar, (unsigned)rows * rowbytes);
+  __syncwarp();
+  for (int r = lane; r < rows; r += 32) {
+    const int ti = contig ? r : r / n;
+    const int j = contig ? 0 : r - ti * n;
+    const int64_t t = bid + (c0 + ti) * nb;
+    const int64_t o = t / tpo;
+    const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W + (int64_t)j * s;
+    bulk_load(reg + (contig ? ti * W * n : ti * W * n + j * W), src + base, rowbytes, bar);
+  }
+}
+
+// Wait for a region's bulk copies (every thread).  Bounded by time (the
+// barrier limit) and by a spin count; a timeout is recorded in the status word.
+__device__ __forceinline__ void wait_region(const Bufs& B, uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return;
+  const uint64_t t0 = global_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    ++spins;
+    if ((spins & 63u) == 0 && (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS)) {
+      if (threadIdx.x == 0) atomicExch(B.status, ST_TIMEOUT);
+      break;
+    }
+  }
+}
+
 template <typename T, bool INV, int KIND>
 __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const Smem<typename VT<T>::v>& S,
                          int res_in) {
@@ -659,6 +769,7 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   const AxisPlan& ax = P.ax[A.l];
   const int n = ax.n, W = ax.W, D = P.D;
   const bool contig = (A.l == D - 1);
+  const int wsh = contig ? 0 : __ffs(W) - 1;   // W is a power of two
   const int64_t s = ax.stride;
   const int64_t tpo = contig ? 1 : s / W;  // tiles per outer index
   const int64_t ws = contig ? n : 1;       // element step between lines of a tile
@@ -684,67 +795,103 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   V* dst = (V*)A.dst;
   int res = -1;
   const int chunk = A.from_smem || A.keep ? (int)mine : ax.tpc;
+  // HBM-streamed passes: chunk k+1 is copied by the TMA engine into a third
+  // region while chunk k is transformed and written back.
+  const bool stream = !P.resident && !A.from_smem && !A.keep && mine > 0;
+  int rd = 0, rt = 1, rf = 2;  // data, temporary and prefetch regions
+  unsigned parity = 0;          // one phase bit per region
+  if (stream) {
+    parity = *S.mphase;
+    if (threadIdx.x < 32) issue_chunk(ax, contig, src, 0, (int)(mine < chunk ? mine : chunk), S.reg[rd], S.mbar + rd);
+  }
   for (int64_t c0 = 0; c0 < mine; c0 += chunk) {
     const int nt = (int)(mine - c0 < chunk ? mine - c0 : chunk);
     const int cnt = nt * W * n;
+    if (stream && c0 + chunk < mine && threadIdx.x < 32) {
+      const int64_t c1 = c0 + chunk;
+      issue_chunk(ax, contig, src, c1, (int)(mine - c1 < chunk ? mine - c1 : chunk), S.reg[rf], S.mbar + rf);
+    }
+    // per-tile offsets (one 64-bit division per tile, not per element) and,
+    // for the fused reductions, the multi-index of every line of the chunk
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+      const int64_t t = bid + (c0 + k) * nb;
+      const int64_t o = t / tpo;
+      S.tb[k] = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
+    }
+    if (A.red != RED_NONE) {
+      for (int kw = threadIdx.x; kw < nt * W; kw += blockDim.x) {
+        const int k = kw / W, w = kw - k * W;
+        const int64_t t = bid + (c0 + k) * nb;
+        const int64_t o = t / tpo;
+        int idx[MAXD];
+        const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
+        const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
+        decode(P, A.l, lo, li, 0, idx);
+        for (int a = 0; a < D; ++a) S.li[kw * D + a] = (uint16_t)idx[a];
+      }
+    }
     V* cur;
+    V* oth;
     if (A.from_smem) {
       cur = S.reg[res_in];
+      oth = S.reg[res_in ^ 1];
+    } else if (stream) {
+      wait_region(B, S.mbar + rd, (parity >> rd) & 1u);
+      parity ^= 1u << rd;
+      cur = S.reg[rd];
+      oth = S.reg[rt];
     } else {
       // up to LOADS independent global loads in flight per thread before the
       // shared-memory stores (one L2 round trip instead of one per element)
-      constexpr int LOADS = 4;
+      constexpr int LOADS = 8;
+      __syncthreads();  // S.tb ready
       cur = S.reg[0];
+      oth = S.reg[1];
+      const Div16 divWn((unsigned)(W * n)), divn((unsigned)n);
       for (int e0 = threadIdx.x; e0 < cnt; e0 += LOADS * blockDim.x) {
         V vals[LOADS];
-        int dsti[LOADS];
 #pragma unroll
         for (int u = 0; u < LOADS; ++u) {
           const int e = e0 + u * blockDim.x;
-          dsti[u] = -1;
           if (e < cnt) {
-            const int ti = e / (W * n);
+            const int ti = (int)divWn((unsigned)e);
             const int rem = e - ti * W * n;
-            int w, j;
-            if (contig) { w = rem / n; j = rem - w * n; }
-            else { j = rem / W; w = rem - j * W; }
-            const int64_t t = bid + (c0 + ti) * nb;
-            const int64_t o = t / tpo;
-            const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
-            vals[u] = __ldcg(src + base + j * es + w * ws);
-            dsti[u] = (ti * W + w) * n + j;
+            const int w = contig ? (int)divn((unsigned)rem) : rem & (W - 1);
+            const int j = contig ? rem - w * n : rem >> wsh;
+            vals[u] = __ldcg(src + S.tb[ti] + j * es + w * ws);
           }
         }
 #pragma unroll
-        for (int u = 0; u < LOADS; ++u)
-          if (dsti[u] >= 0) cur[dsti[u]] = vals[u];
+        for (int u = 0; u < LOADS; ++u) {
+          const int e = e0 + u * blockDim.x;
+          if (e < cnt) cur[e] = vals[u];
+        }
       }
     }
     __syncthreads();
     if (A.fft) {
-      cur = stockham<INV>(cur, cur == S.reg[0] ? S.reg[1] : S.reg[0], nt * W, ax, tw, pre);
+      cur = stockham<INV>(cur, oth, nt * W, ax, tw, pre, wsh);
     } else if (pre) {
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) cur[e] = cmul(cur[e], pre[e % n]);
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+        cur[e] = cmul(cur[e], pre[contig ? e % n : (e % (W * n)) >> wsh]);
       __syncthreads();
     }
 
-    // epilogue
+    // epilogue: element e of the chunk is tile ti, point j, line w
+    const Div16 divWn((unsigned)(W * n)), divn((unsigned)n);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int ti = e / (W * n);
+      const int ti = (int)divWn((unsigned)e);
       const int rem = e - ti * W * n;
-      int w, j;
-      if (contig) { w = rem / n; j = rem - w * n; }
-      else { j = rem / W; w = rem - j * W; }
-      const int64_t t = bid + (c0 + ti) * nb;
-      const int64_t o = t / tpo;
-      const int si = (ti * W + w) * n + j;
-      V v = cur[si];
+      const int w = contig ? (int)divn((unsigned)rem) : rem & (W - 1);
+      const int j = contig ? rem - w * n : rem >> wsh;
+      V v = cur[e];
       if (post) v = cmul(v, post[j]);
       if (A.red != RED_NONE) {
         int idx[MAXD];
-        const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
-        const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
-        decode(P, A.l, lo, li, j, idx);
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a)
+          if (a < D) idx[a] = S.li[(ti * W + w) * D + a];
+        idx[A.l] = j;
         // |value|^2: FP64 for FP64 storage; FP32 product, FP64 accumulation otherwise
         bool handled = false;
         if constexpr (sizeof(T) == 4) {
@@ -758,57 +905,66 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
           }
         }
         if (!handled) {
-        double w2;
-        if constexpr (sizeof(T) == 8) w2 = fma((double)v.x, (double)v.x, (double)v.y * (double)v.y);
-        else w2 = (double)fmaf(v.x, v.x, v.y * v.y);
-        acc[0] += w2;
-        if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
-          double te = 0;
-#pragma unroll
-          for (int a = 0; a < MAXD; ++a)
-            if (a < D) {
-              acc[1 + a] = fma(S.tc[P.ax[a].toff + idx[a]], w2, acc[1 + a]);
-              if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
-            }
-          if (A.red == RED_OBS_KIN) acc[D + 1] = fma(te, w2, acc[D + 1]);
-        } else {
-          double th, g[MAXD];
-          vpoint<KIND>(P, S.tv, idx, sgh, th, g);
-          if (A.red == RED_V) {
+          double w2;
+          if constexpr (sizeof(T) == 8) w2 = fma((double)v.x, (double)v.x, (double)v.y * (double)v.y);
+          else w2 = (double)fmaf(v.x, v.x, v.y * v.y);
+          acc[0] += w2;
+          if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
+            double te = 0;
 #pragma unroll
             for (int a = 0; a < MAXD; ++a)
-              if (a < D) acc[1 + a] = fma(g[a], w2, acc[1 + a]);
-            if constexpr (sizeof(T) == 8) {
-              double sn, cs;
-              expi_tab(th, S.sct, sn, cs);
-              v = V{fma(v.x, cs, -v.y * sn), fma(v.x, sn, v.y * cs)};
-            } else {
-              // FP64 phase argument reduced modulo 2 pi (two-word 2 pi), then
-              // FP32 sine and cosine of the reduced angle (|r| <= pi)
-              const double kk = rint(th * 0.15915494309189535);
-              double r = fma(-kk, 6.283185307179586, th);
-              r = fma(-kk, 2.4492935982947064e-16, r);
-              float sn, cs;
-              sincosf((float)r, &sn, &cs);
-              v = V{fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs)};
-            }
-          } else {  // observables: <x> and <V>
+              if (a < D) {
+                acc[1 + a] = fma(S.tc[P.ax[a].toff + idx[a]], w2, acc[1 + a]);
+                if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
+              }
+            if (A.red == RED_OBS_KIN) acc[D + 1] = fma(te, w2, acc[D + 1]);
+          } else {
+            double th, g[MAXD];
+            vpoint<KIND>(P, S.tv, idx, sgh, th, g);
+            if (A.red == RED_V) {
 #pragma unroll
-            for (int a = 0; a < MAXD; ++a)
-              if (a < D) acc[1 + a] = fma(fma(S.tc[P.ax[a].toff + idx[a]], P.dq[a], S.sc[SC_Q + a]), w2, acc[1 + a]);
-            acc[D + 1] = fma(th, w2, acc[D + 1]);
+              for (int a = 0; a < MAXD; ++a)
+                if (a < D) acc[1 + a] = fma(g[a], w2, acc[1 + a]);
+              if constexpr (sizeof(T) == 8) {
+                double sn, cs;
+                expi_tab(th, S.sct, sn, cs);
+                v = V{fma(v.x, cs, -v.y * sn), fma(v.x, sn, v.y * cs)};
+              } else {
+                // FP64 phase argument reduced modulo 2 pi (two-word 2 pi), then
+                // FP32 sine and cosine of the reduced angle (|r| <= pi)
+                const double kk = rint(th * 0.15915494309189535);
+                double r = fma(-kk, 6.283185307179586, th);
+                r = fma(-kk, 2.4492935982947064e-16, r);
+                float sn, cs;
+                sincosf((float)r, &sn, &cs);
+                v = V{fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs)};
+              }
+            } else {  // observables: <x> and <V>
+#pragma unroll
+              for (int a = 0; a < MAXD; ++a)
+                if (a < D)
+                  acc[1 + a] = fma(fma(S.tc[P.ax[a].toff + idx[a]], P.dq[a], S.sc[SC_Q + a]), w2, acc[1 + a]);
+              acc[D + 1] = fma(th, w2, acc[D + 1]);
+            }
           }
         }
-        }
       }
-      if (A.keep) cur[si] = v;
-      else if (dst) {
-        const int64_t base = contig ? t * W * n : o * n * s + (t - o * tpo) * W;
-        __stcg(dst + base + j * es + w * ws, v);
-      }
+      if (A.keep) cur[e] = v;
+      else if (dst) __stcg(dst + S.tb[ti] + j * es + w * ws, v);
     }
     __syncthreads();
-    res = cur == S.reg[0] ? 0 : 1;
+    if (stream) {
+      // the prefetched region holds the next chunk; the other two are free
+      const int nd = rf;
+      rf = rd;
+      rd = nd;
+    } else {
+      res = cur == S.reg[0] ? 0 : (cur == S.reg[1] ? 1 : 2);
+    }
+  }
+  if (stream) {
+    if (threadIdx.x == 0) *S.mphase = parity;
+    __syncthreads();
   }
   if (A.red != RED_NONE) {
     if constexpr (sizeof(T) == 4) {
@@ -821,6 +977,16 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
     block_partials(B, S, A.slot, acc, nv);
   }
   return res;
+}
+
+// One-time set-up of the streamed-pass mbarriers (kernel start, before use).
+template <typename V> __device__ void init_mbarriers(const Smem<V>& S) {
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < 3; ++r) mbar_init(S.mbar + r);
+    *S.mphase = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
 }
 
 // Store tiles of axis D-1 that are resident in smem region `res` to psi.
@@ -941,7 +1107,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     sc[SC_P + threadIdx.x] = __ldcg(B.ctrl + 8 + threadIdx.x);
   }
   load_tables(P, B, S, LT_TW | LT_A | LT_C | LT_SCT);
-  __syncthreads();
+  init_mbarriers(S);
   const double* gam = B.gamma;
   int res = -1;
   bool kept = false;
@@ -1086,7 +1252,7 @@ __global__ void __launch_bounds__(THREADS)
   if (threadIdx.x < P.D) S.sc[SC_Q + threadIdx.x] = B.ctrl[threadIdx.x];
   if (threadIdx.x == 0) S.sc[SC_SGH] = 1.0;
   load_tables(P, B, S, LT_TW | LT_A | LT_C | LT_V | LT_E | LT_SCT);
-  __syncthreads();
+  init_mbarriers(S);
   PassArgs a{};
   a.l = l;
   if (mode == 0) {  // forward transform pass; kinetic moments on axis 0
@@ -1099,6 +1265,34 @@ __global__ void __launch_bounds__(THREADS)
     a.src = B.psi; a.dst = nullptr;
   }
   axis_pass<T, false, KIND>(P, B, a, S, -1);
+}
+
+// Separable state u^J = prod_l f_l[j_l] from per-axis factors staged in
+// B.tabK (FP64 products, stored in the context's precision).  One row of the
+// contiguous axis per thread at a time.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_set_product(const __grid_constant__ Plan P,
+                                                          const __grid_constant__ Bufs B) {
+  using V = typename VT<T>::v;
+  const int D = P.D;
+  const int nl = P.ax[D - 1].n;
+  const int64_t rows = P.npts / nl;
+  const double2* f = B.tabK;
+  V* u = (V*)B.psi;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(1.0, 0.0);
+    uint64_t rem = (uint64_t)r;
+    for (int a = D - 2; a >= 0; --a) {
+      const uint64_t n = (uint64_t)P.N[a];
+      const double2 v = f[P.ax[a].toff + (int)(rem % n)];
+      rem /= n;
+      acc = cmul(acc, v);
+    }
+    for (int j = 0; j < nl; ++j) {
+      const double2 v = cmul(acc, f[P.ax[D - 1].toff + j]);
+      u[r * nl + j] = from_d2<V>(v);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1139,6 +1333,7 @@ void* obs_kernel(int prec, int kind) {
 }
 
 void* init_tables_kernel() { return (void*)k_init_tables; }
+void* set_product_kernel(int prec) { return prec ? (void*)k_set_product<float> : (void*)k_set_product<double>; }
 void* obs_tables_kernel() { return (void*)k_obs_tables; }
 
 }  // namespace mgk

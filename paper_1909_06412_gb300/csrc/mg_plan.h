@@ -41,6 +41,8 @@ struct Plan {
   int tab_total;         // sum of N_l
   int region_bytes;      // bytes of each of the two smem data regions
   int smem_bytes;        // dynamic smem per CTA
+  int max_tiles;         // most tiles in one smem chunk (any axis)
+  int max_lines;         // most lines in one smem chunk (any axis)
   int64_t npts;
   int64_t N[MAXD];
   double dq[MAXD], dp[MAXD], minv[MAXD], hbar;

