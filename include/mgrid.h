@@ -123,6 +123,25 @@ mg_status mg_get_observables(mg_ctx* ctx, double* norm, double* energy, double* 
 /* Synchronise the context's stream and report any pending device status. */
 mg_status mg_sync(mg_ctx* ctx);
 
+/* Reverse-mode derivative of the last mg_propagate call, by the reversible
+ * adjoint: the context's state must be the final state of that call (same
+ * n_steps, dt, scheme, split, grid_motion).  Each substep of Sec. II.G is undone
+ * by the same substep at the negated time (exact time reversibility), so no
+ * trajectory is stored, and its vector-Jacobian product is applied to the
+ * cotangent on the way.  Convention: for a real objective J,
+ * ubar = dJ/dRe u + i dJ/dIm u (u the scaled state in d_psi), qbar = dJ/dq,
+ * pbar = dJ/dp.
+ *  - d_ubar: device complex128 buffer like d_psi; in: ubar at the final time,
+ *    out: ubar at the initial time.  qbar, pbar: host, D doubles, in/out.
+ *  - theta_bar: host, out, ntheta values dJ/d(Dm, a, beta, A) for
+ *    MG_POT_ATOM_DIATOM (ntheta = 4); ntheta = 0 for MG_POT_HARMONIC.
+ *  - On return the context holds the regenerated initial state and time.
+ *  - FP64 contexts whose state and cotangent fit in the CTAs' shared memory;
+ *    harmonic or atom-diatom potential.  MG_ERR_UNSUPPORTED otherwise.
+ *  - Synchronises the context's stream. */
+mg_status mg_adjoint(mg_ctx* ctx, int64_t n_steps, double dt, const char* scheme, int split, int grid_motion,
+                     void* d_ubar, double* qbar, double* pbar, double* theta_bar, int ntheta);
+
 /* Number of kernels this context has launched so far. */
 int64_t mg_kernel_launches(const mg_ctx* ctx);
 

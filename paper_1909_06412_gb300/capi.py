@@ -53,8 +53,9 @@ def lib():
         L.mg_morse_mean.restype = d
         L.mg_status_string.argtypes = [i32]
         L.mg_status_string.restype = ctypes.c_char_p
+        L.mg_adjoint.argtypes = [vp, i64, d, ctypes.c_char_p, i32, i32, vp, vp, vp, vp, i32]
         for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
-                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync"):
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -142,6 +143,8 @@ class Propagator:
     def set_potential(self, kind, params):
         p = _f64(params)
         _check(lib().mg_set_potential(self._h, kind, _ptr(p), p.size), "mg_set_potential")
+        self._pot_kind = kind
+        self._pot_params = [float(v) for v in p]
 
     def set_state(self, psi, q, p, t=0.0):
         q, p = _f64(q, self.D), _f64(p, self.D)
@@ -181,6 +184,27 @@ class Propagator:
         mq, mp = np.empty(self.D), np.empty(self.D)
         _check(lib().mg_get_observables(self._h, _ptr(n), _ptr(e), _ptr(mq), _ptr(mp)), "mg_get_observables")
         return float(n[0]), float(e[0]), mq, mp
+
+    def adjoint(self, n_steps, dt, scheme, ubar, qbar, pbar, split=MG_TVT, grid_motion=MG_GRID_ADAPTIVE):
+        """Cotangents at the start of the last propagate(n_steps, dt, scheme, ...)
+        call given those at its end (see mg_adjoint).  ubar: complex array of the
+        grid's shape (numpy) or a CUDA complex128 tensor; returns
+        (ubar0 as numpy complex128, qbar0, pbar0, thetabar); the context's state
+        is rewound to the start of that call."""
+        torch = self.torch
+        if isinstance(ubar, torch.Tensor):
+            ub = ubar.detach().to(self.device, torch.complex128).contiguous().clone()
+        else:
+            ub = torch.from_numpy(np.ascontiguousarray(ubar, dtype=np.complex128)).to(self.device)
+        if ub.numel() != int(np.prod(self.N)):
+            raise ValueError("ubar must have one complex value per grid point")
+        qb, pb = _f64(qbar, self.D).copy(), _f64(pbar, self.D).copy()
+        nth = 4 if getattr(self, "_pot_kind", None) == MG_POT_ATOM_DIATOM else 0
+        th = np.zeros(max(nth, 1))
+        rc = lib().mg_adjoint(self._h, int(n_steps), float(dt), scheme.encode(), split, grid_motion,
+                              ctypes.c_void_p(ub.data_ptr()), _ptr(qb), _ptr(pb), _ptr(th), nth)
+        _check(rc, "mg_adjoint")
+        return ub.cpu().numpy().reshape(self.N), qb, pb, th[:nth]
 
     @property
     def launches(self):

@@ -18,6 +18,7 @@ void* obs_kernel(int prec, int kind);
 void* init_tables_kernel();
 void* obs_tables_kernel();
 void* set_product_kernel(int prec);
+void* adjoint_kernel(int kind);
 }  // namespace mgk
 
 using namespace mgk;
@@ -47,10 +48,11 @@ Layout layout_for(int D, const int64_t* N, int precision) {
     o = align256(o + bytes);
     return at;
   };
-  L.ctrl = put(32 * sizeof(double));
+  L.ctrl = put(CTRL * sizeof(double));
   L.bar = put(64 * sizeof(unsigned));
   L.status = put(sizeof(int));
-  L.part = put(2ull * MAXBLOCKS * PSTRIDE * sizeof(double));
+  // two slots of per-CTA records; the adjoint's records are 32 doubles
+  L.part = put(2ull * MAXBLOCKS * 32 * sizeof(double));
   L.tw = put(tt * sizeof(double2));
   L.tabA = put(tt * sizeof(double2));
   L.tabAi = put(tt * sizeof(double2));
@@ -92,13 +94,13 @@ void radix_plan(int n, AxisPlan& ax, int rmax = 8) {
 }
 
 size_t smem_for(const Plan& P) {
-  // must match carve() in mg_kernels.cu
+  // must match carve() in mg_device.cuh
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
   const size_t TT = (size_t)P.tab_total;
   size_t s = 4 * r16(vs * TT) + r16(sizeof(double) * NVCOL * TT) + 2 * r16(sizeof(double) * TT) +
-             r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (P.D + 2)) +
-             r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * 40) +
+             r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (3 * P.D + 5)) +
+             r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) +
              (P.resident ? 2 : 3) * r16((size_t)P.region_bytes) + r16(sizeof(uint64_t) * 3) +
              r16(sizeof(unsigned) * 4) + r16(sizeof(int64_t) * P.max_tiles) +
              r16(sizeof(uint16_t) * P.max_lines * P.D);
@@ -723,6 +725,81 @@ mg_status mg_get_observables(mg_ctx* c, double* norm, double* energy, double* me
     if (mean_q) mean_q[a] = v[1 + a] / v[0];
     if (mean_p) mean_p[a] = ctrl[8 + a] + P.dp[a] * k[1 + a] / k[0];
   }
+  return MG_OK;
+}
+
+mg_status mg_adjoint(mg_ctx* c, int64_t n_steps, double dt, const char* scheme, int split, int grid_motion,
+                     void* d_ubar, double* qbar, double* pbar, double* theta_bar, int ntheta) {
+  if (!c || !d_ubar || !qbar || !pbar || n_steps < 0 || !std::isfinite(dt)) return MG_ERR_ARG;
+  if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
+    return MG_ERR_ARG;
+  if (((uintptr_t)d_ubar & 15)) return MG_ERR_ARG;
+  if (!scheme_coeffs(scheme, c->gam)) return MG_ERR_ARG;
+  if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
+  const Plan& P = c->P;
+  const int nth = P.pot_kind == MG_POT_ATOM_DIATOM ? 4 : 0;
+  if (P.prec != MG_FP64 || !P.resident) return MG_ERR_UNSUPPORTED;
+  if (P.pot_kind != MG_POT_HARMONIC && P.pot_kind != MG_POT_ATOM_DIATOM) return MG_ERR_UNSUPPORTED;
+  if (ntheta != nth || (nth > 0 && !theta_bar)) return MG_ERR_ARG;
+  for (int a = 0; a < P.D; ++a)
+    if (!std::isfinite(qbar[a]) || !std::isfinite(pbar[a])) return MG_ERR_ARG;
+  if (n_steps == 0) {
+    for (int k = 0; k < nth; ++k) theta_bar[k] = 0.0;
+    return MG_OK;
+  }
+  // the dual (state + cotangent) passes need two more shared-memory regions
+  const size_t smem = (size_t)P.smem_bytes + 2 * (((size_t)P.region_bytes + 15) & ~size_t(15));
+  void* fn = adjoint_kernel(P.pot_kind);
+  if (!fn || smem > 227 * 1024) return MG_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return MG_ERR_CUDA;
+  int occ = 0, dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, THREADS, smem) != cudaSuccess)
+    return MG_ERR_CUDA;
+  if (occ * sms < P.nblocks) return MG_ERR_UNSUPPORTED;
+  double norm = 0;
+  mg_status s = mg_get_observables(c, &norm, nullptr, nullptr, nullptr);
+  if (s != MG_OK) return s;
+  AdjRun AR{};
+  AR.R.n_steps = n_steps;
+  AR.R.S = (int)c->gam.size();
+  AR.R.dt = dt;
+  AR.R.split = split;
+  AR.R.motion = grid_motion;
+  AR.R.lead_v = split != MG_TVT;
+  AR.R.n_units = (split == MG_TVT) ? n_steps * AR.R.S + 1 : n_steps * AR.R.S;
+  AR.ubar = d_ubar;
+  AR.ntheta = nth;
+  AR.norm = norm;
+  double cb[16] = {0};
+  for (int a = 0; a < P.D; ++a) {
+    cb[a] = qbar[a];
+    cb[8 + a] = pbar[a];
+  }
+  s = cuda_ok(cudaMemcpyAsync(c->B.ctrl + 20, cb, sizeof(cb), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK)
+    s = cuda_ok(cudaMemcpyAsync((void*)c->B.gamma, c->gam.data(), c->gam.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
+  if (s != MG_OK) return s;
+  void* args[] = {&c->P, &c->B, &AR};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(P.nblocks), dim3(THREADS), args, smem, c->stream);
+  c->launches++;
+  if (e != cudaSuccess) return MG_ERR_CUDA;
+  s = read_status(c);
+  if (s != MG_OK) return s;
+  double ctrl[CTRL];
+  if (cudaMemcpy(ctrl, c->B.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+  for (int a = 0; a < P.D; ++a) {
+    c->q[a] = ctrl[a];
+    c->p[a] = ctrl[8 + a];
+    qbar[a] = ctrl[20 + a];
+    pbar[a] = ctrl[28 + a];
+  }
+  for (int k = 0; k < nth; ++k) theta_bar[k] = ctrl[36 + k];
+  c->t -= (double)n_steps * dt;
   return MG_OK;
 }
 

@@ -13,6 +13,8 @@ constexpr int PSTRIDE = 16;    // doubles per CTA partial-sum record
 constexpr int NVCOL = 5;       // potential-table columns per axis
 constexpr int MAX_STAGES = 625;
 constexpr int THREADS = 256;   // threads per CTA of every kernel
+constexpr int SCALARS = 112;   // double slots of per-CTA scalar state in shared memory
+constexpr int CTRL = 64;       // doubles of the control block in the workspace
 
 enum { POT_HARMONIC = 0, POT_ATOM_DIATOM = 1, POT_HENON_HEILES = 2, POT_SECREST_JOHNSON = 3 };
 enum { SPLIT_TVT = 0, SPLIT_VTV = 1, SPLIT_TV = 2 };
@@ -77,6 +79,14 @@ struct Run {
   int64_t n_steps;
   int split, motion, S, lead_v;
   double dt;
+};
+
+// One adjoint launch (the propagation it reverses, and the cotangent buffer).
+struct AdjRun {
+  Run R;
+  void* ubar;            // device complex128 cotangent of psi (in: at t_end; out: at t_start)
+  int ntheta;            // potential parameters differentiated (4 for atom-diatom)
+  double norm;           // sum |u|^2, an invariant of the propagation
 };
 
 }  // namespace mgk
