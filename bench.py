@@ -37,6 +37,7 @@ POT = [0.17, 1.0, 1.4, 5.0, 1.8]  # Dm, a, re, A, beta
 SCHEME, STAGES, DT = "yoshida4", 3, 1.0
 STEPS_PER_CALL = 100
 CPU_SAMPLE_STEPS = 30
+ADJ_STEPS = 200
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM bytes (read + write) of one propagate launch, from an ncu capture of
@@ -321,6 +322,52 @@ def mixed_precision_leg(mgmod, torch, dev, args, flush):
     }
 
 
+def adjoint_leg(mgmod, torch, dev):
+    """Cost of the reversible adjoint against the forward propagation it
+    differentiates, on the two gradient workloads (FP64, sixth-order triple
+    jump, 9 TVT stages per step): the atom-diatom model on a 128 x 128 grid
+    (dR = 0.16, dr = 0.08, dt = 1 a.u.) and the 3D harmonic oscillator on a
+    64^3 grid (dq = 0.3, dt = 0.01).  Each is timed over one forward call of
+    ADJ_STEPS steps and the adjoint call that rewinds it."""
+    out = []
+    rbar = mgmod.mg_morse_mean(POT[0], POT[1], POT[2], 0.5 * AMU)
+    om = np.array([1.0, 1.2, 1.5])
+    cases = [
+        ("atom-diatom 128x128 FP64, yoshida6, dt=1 a.u.", (128, 128), (0.16, 0.08), MINV,
+         mgmod.MG_POT_ATOM_DIATOM, POT, initial(mgmod)[0], [8.0, rbar], [-10.0, 0.0], 1.0),
+        ("3D harmonic 64^3 FP64, yoshida6, dt=0.01", (64, 64, 64), (0.3,) * 3, (1.0, 1.0, 1.0),
+         mgmod.MG_POT_HARMONIC, list(np.diag(om ** 2).ravel()) + [0.0] * 3,
+         [("gauss", q, p, w ** -0.5) for q, p, w in zip((1.0, -0.5, 0.8), (0.0, 0.5, -0.3), om)],
+         (1.0, -0.5, 0.8), (0.0, 0.5, -0.3), 0.01),
+    ]
+    for name, N, dq, minv, kind, pot, fac, q0, p0, dt in cases:
+        g = mgmod.Propagator(N, dq, minv=minv, device=dev)
+        g.set_potential(kind, pot)
+        g.set_separable(fac, q0, p0)
+        D = len(N)
+        ub = torch.zeros(int(np.prod(N)), dtype=torch.complex128, device=dev)
+        qb, pb = np.eye(D)[0], np.zeros(D)
+        # warm-up pair, then the timed pair
+        g.propagate(2, dt, "yoshida6")
+        g.adjoint(2, dt, "yoshida6", ub, qb, pb)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(g.stream)
+        g.propagate(ADJ_STEPS, dt, "yoshida6")
+        ev[1].record(g.stream)
+        g.sync()
+        g.adjoint(ADJ_STEPS, dt, "yoshida6", ub, qb, pb)
+        ev[2].record(g.stream)
+        g.sync()
+        tf, ta = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+        out.append({"workload": name, "steps": ADJ_STEPS, "forward_s": tf, "adjoint_s": ta,
+                    "adjoint_over_forward": ta / tf,
+                    "note": "adjoint_s includes the host-side norm readout and cotangent upload of mg_adjoint"})
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +462,7 @@ def main():
     cpu, err = cpu_baseline_and_error(mg, torch)
     mixed = mixed_precision_leg(mg, torch, dev, args, flush)
     others = other_workloads(mg, torch, dev, flush)
+    adj = adjoint_leg(mg, torch, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -441,6 +489,7 @@ def main():
         },
         "mixed_precision": mixed,
         "other_workloads": others,
+        "adjoint": adj,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,

@@ -183,3 +183,71 @@ def test_autograd_function(mg):
     assert np.allclose(q0t.grad.numpy(), qbo, rtol=1e-9, atol=1e-10)
     assert np.allclose(p0t.grad.numpy(), pbo, rtol=1e-9, atol=1e-10)
     assert np.allclose(th.grad.numpy(), tho, rtol=1e-8, atol=1e-10)
+
+
+def test_gradient_3d_harmonic_vs_finite_differences(mg):
+    # 64^3 grid, dq = 0.3, omega = (1, 1.2, 1.5), unit masses, sixth-order
+    # triple jump, dt = 0.01; initial widths sigma_i = s / sqrt(omega_i), s = 1
+    N, dq = (64, 64, 64), (0.3, 0.3, 0.3)
+    om = np.array([1.0, 1.2, 1.5])
+    pot = list(np.diag(om ** 2).ravel()) + [0.0] * 3
+    steps, dt, scheme = 100, 0.01, "yoshida6"
+    T = steps * dt
+    q0n, p0n = np.array([1.0, -0.5, 0.8]), np.array([0.0, 0.5, -0.3])
+    # target: coherent state at the classical point at T, shifted by 0.6 in q_1
+    # (a shift of 0.3 leaves |overlap|^2 = e^{-0.045}, above 0.9)
+    qt = q0n * np.cos(om * T) + p0n / om * np.sin(om * T) + np.array([0.6, 0.0, 0.0])
+    pt = p0n * np.cos(om * T) - q0n * om * np.sin(om * T)
+
+    def make(q0, p0, s):
+        g = mg.Propagator(N, dq)
+        g.set_potential(mg.MG_POT_HARMONIC, pot)
+        g.set_separable([("gauss", q0[l], p0[l], s / np.sqrt(om[l])) for l in range(3)], q0, p0)
+        return g
+
+    ys = [(np.arange(N[l]) - N[l] / 2) * dq[l] for l in range(3)]
+
+    def objective(g):
+        u = g.psi.view(torch.complex128).cpu().numpy().reshape(N)
+        _, q, p, _ = g.get_state(want_psi=False)
+        X = np.meshgrid(*[q[l] + ys[l] for l in range(3)], indexing="ij")
+        w = np.abs(u) ** 2
+        n = w.sum()
+        mq = (X[0] * w).sum() / n
+        logf = sum(0.25 * np.log(om[l] / np.pi) - 0.5 * om[l] * (X[l] - qt[l]) ** 2 + 1j * pt[l] * (X[l] - qt[l])
+                   for l in range(3))
+        f = np.exp(logf) * np.sqrt(np.prod(dq))
+        ov = np.vdot(f, u)
+        J = mq + abs(ov) ** 2
+        ub = 2 * (X[0] - mq) / n * u + 2 * ov * f
+        qb = np.array([float(l == 0) + 2 * np.real(np.conj(ov) * np.vdot((-om[l] * (X[l] - qt[l]) + 1j * pt[l]) * f, u))
+                       for l in range(3)])
+        return J, ub, qb, 1e-3 < abs(ov) ** 2 < 0.9
+
+    def J_of(q0, p0, s):
+        g = make(q0, p0, s)
+        g.propagate(steps, dt, scheme)
+        return objective(g)[0]
+
+    g = make(q0n, p0n, 1.0)
+    u0 = g.psi.view(torch.complex128).cpu().numpy().reshape(N).copy()
+    g.propagate(steps, dt, scheme)
+    J, ubT, qbT, ok = objective(g)
+    assert ok
+    ub0, qb0, pb0, _ = g.adjoint(steps, dt, scheme, ubT, qbT, np.zeros(3))
+    Y = np.meshgrid(*ys, indexing="ij")
+    grads = {}
+    for l in range(3):
+        grads[f"q0_{l}"] = qb0[l]
+        grads[f"p0_{l}"] = pb0[l] + np.real(np.vdot(ub0, 1j * Y[l] * u0))
+    dlog_s = sum(-0.5 + om[l] * Y[l] ** 2 for l in range(3))  # at s = 1
+    grads["s"] = np.real(np.vdot(ub0, dlog_s * u0))
+    h = 1e-5
+    fd = {}
+    for l in range(3):
+        e = np.eye(3)[l] * h
+        fd[f"q0_{l}"] = (J_of(q0n + e, p0n, 1.0) - J_of(q0n - e, p0n, 1.0)) / (2 * h)
+        fd[f"p0_{l}"] = (J_of(q0n, p0n + e, 1.0) - J_of(q0n, p0n - e, 1.0)) / (2 * h)
+    fd["s"] = (J_of(q0n, p0n, 1.0 + h) - J_of(q0n, p0n, 1.0 - h)) / (2 * h)
+    for name in fd:
+        assert abs(grads[name] - fd[name]) < 1e-6 * max(1.0, abs(fd[name])), (name, grads[name], fd[name])
