@@ -179,6 +179,61 @@ mg_status mg_propagate_noalloc(int D, const int64_t* N, const double* dq, const 
                                double* p, int64_t n_steps, double dt, const char* scheme, int split,
                                int grid_motion, void* cuda_stream);
 
+/* ---- Batched propagation ---------------------------------------------------
+ * Many independent grids of uneven sizes and potentials advanced by one
+ * persistent launch.  The paper propagates one wavepacket at a time; the
+ * batch applies the same integrator (the substeps of Sec. II.G composed as in
+ * eq:comp_TVT) to every problem independently, with results equal to
+ * mg_propagate on each context up to the order of floating-point sums.
+ *
+ * Each problem is an existing context (mg_create + mg_set_potential + a
+ * state), which keeps its own state buffer and workspace; the batch adds only
+ * the launch.  A team of `cluster` CTAs (a thread-block cluster) propagates
+ * one problem at a time; problems are dealt to teams longest first.  The
+ * launch (upload of the run parameters + the kernel) is captured once into a
+ * CUDA graph at mg_batch_create and replayed by every mg_batch_propagate. */
+typedef struct mg_batch mg_batch;
+
+/* Device workspace bytes a batch of `nprob` problems needs (0 if nprob < 1). */
+size_t mg_batch_workspace_bytes(int nprob);
+
+/* Create a batch over nprob contexts.
+ *  - ctxs: nprob contexts, all of one precision, created on one CUDA stream
+ *    (the batch runs on it), with a potential and a state set, and at most 3
+ *    axes each.  A context may appear once only.  The contexts must outlive
+ *    the batch.
+ *  - cluster: CTAs per team, 1, 2, 4 or 8 (0 = 2).
+ *  - tile_bytes: NULL or nprob targets for the bytes of one FFT tile of that
+ *    problem (0 = default); radix_max: NULL or nprob largest Stockham radix
+ *    (0 = default, else 2, 4 or 8).  These are the knobs the autotuner sets.
+ *  - d_work: caller-owned device buffer of mg_batch_workspace_bytes(nprob)
+ *    bytes, 256-byte aligned; the batch also allocates a small pinned host
+ *    block for the run parameters.
+ * Returns MG_ERR_STATE if a context lacks a potential or a state,
+ * MG_ERR_UNSUPPORTED for contexts with more than 3 axes or a layout that does
+ * not fit in shared memory. */
+mg_status mg_batch_create(mg_batch** out, int nprob, mg_ctx* const* ctxs, int cluster, const int* tile_bytes,
+                          const int* radix_max, void* d_work, size_t work_bytes);
+
+/* Advance every problem by n_steps of the named scheme with its own time step
+ * dt[i] (nprob host doubles); split and grid_motion as in mg_propagate, for
+ * all problems.  Potentials changed through mg_set_potential since the last
+ * call are picked up.  Asynchronous on the contexts' stream: per-problem
+ * failures (non-finite reductions, diverging centres) are reported by
+ * mg_batch_sync and by each context's next synchronising call. */
+mg_status mg_batch_propagate(mg_batch* batch, int64_t n_steps, const double* dt, const char* scheme, int split,
+                             int grid_motion);
+
+/* Wait for the batch; returns the status of the first failed problem (its
+ * index in *first_failed, else -1) or MG_OK. */
+mg_status mg_batch_sync(mg_batch* batch, int* first_failed);
+
+/* Launch shape: CTAs per team, teams, dynamic shared memory per CTA, and the
+ * number of batched launches so far. */
+mg_status mg_batch_info(const mg_batch* batch, int* cluster, int* nteams, int* smem_bytes, int64_t* launches);
+
+mg_status mg_batch_destroy(mg_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,8 +22,9 @@ MG_TVT, MG_VTV, MG_TV = 0, 1, 2
 MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED = 0, 1, 2
 MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON = 0, 1, 2, 3
 
-__all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "MgError", "lib", "mg_workspace_bytes",
-                                                        "mg_morse_mean", "mg_propagate_noalloc"]
+__all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "MgError", "lib", "mg_workspace_bytes",
+                                                        "mg_batch_workspace_bytes", "mg_morse_mean",
+                                                        "mg_propagate_noalloc"]
 
 _lib = None
 
@@ -54,8 +55,17 @@ def lib():
         L.mg_status_string.argtypes = [i32]
         L.mg_status_string.restype = ctypes.c_char_p
         L.mg_adjoint.argtypes = [vp, i64, d, ctypes.c_char_p, i32, i32, vp, vp, vp, vp, i32]
+        L.mg_batch_workspace_bytes.argtypes = [i32]
+        L.mg_batch_workspace_bytes.restype = sz
+        L.mg_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, i32, vp, vp, vp, sz]
+        L.mg_batch_propagate.argtypes = [vp, i64, vp, ctypes.c_char_p, i32, i32]
+        L.mg_batch_sync.argtypes = [vp, vp]
+        L.mg_batch_info.argtypes = [vp, vp, vp, vp, vp]
+        L.mg_batch_destroy.argtypes = [vp]
         for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
-                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint"):
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint",
+                     "mg_batch_create", "mg_batch_propagate", "mg_batch_sync", "mg_batch_info",
+                     "mg_batch_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -209,6 +219,71 @@ class Propagator:
     @property
     def launches(self):
         return int(lib().mg_kernel_launches(self._h))
+
+
+def mg_batch_workspace_bytes(nprob):
+    return int(lib().mg_batch_workspace_bytes(int(nprob)))
+
+
+class Batch:
+    """Many Propagator contexts advanced together by one batched launch
+    (mg_batch_*).  The propagators must share one precision and one stream and
+    stay alive with the batch (it keeps references to them)."""
+
+    def __init__(self, props, cluster=0, tile_bytes=None, radix_max=None):
+        import torch
+
+        self.props = list(props)
+        n = len(self.props)
+        if n == 0:
+            raise ValueError("empty batch")
+        self.n = n
+        self.device = self.props[0].device
+        self.stream = self.props[0].stream
+        ws = mg_batch_workspace_bytes(n)
+        self.work = torch.zeros(ws, dtype=torch.uint8, device=self.device)
+        handles = (ctypes.c_void_p * n)(*[p.handle.value for p in self.props])
+        tb = None if tile_bytes is None else np.ascontiguousarray(tile_bytes, dtype=np.int32)
+        rm = None if radix_max is None else np.ascontiguousarray(radix_max, dtype=np.int32)
+        for a in (tb, rm):
+            if a is not None and a.size != n:
+                raise ValueError("tile_bytes and radix_max take one value per problem")
+        h = ctypes.c_void_p()
+        rc = lib().mg_batch_create(ctypes.byref(h), n, ctypes.cast(handles, ctypes.c_void_p), int(cluster),
+                                   _ptr(tb) if tb is not None else None, _ptr(rm) if rm is not None else None,
+                                   ctypes.c_void_p(self.work.data_ptr()), ws)
+        _check(rc, "mg_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def propagate(self, n_steps, dt, scheme="strang", split=MG_TVT, grid_motion=MG_GRID_ADAPTIVE):
+        """dt: one time step for all problems, or one per problem."""
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n,)))
+        rc = lib().mg_batch_propagate(self._h, int(n_steps), _ptr(d), scheme.encode(), split, grid_motion)
+        _check(rc, "mg_batch_propagate")
+
+    def sync(self):
+        """Wait for the batch; raises MgError naming the first failed problem."""
+        idx = np.full(1, -1, dtype=np.int32)
+        rc = lib().mg_batch_sync(self._h, _ptr(idx))
+        if rc != MG_OK:
+            raise MgError(rc, f"mg_batch_sync (problem {int(idx[0])})")
+
+    def info(self):
+        c, t, s = (np.zeros(1, dtype=np.int32) for _ in range(3))
+        l = np.zeros(1, dtype=np.int64)
+        _check(lib().mg_batch_info(self._h, _ptr(c), _ptr(t), _ptr(s), _ptr(l)), "mg_batch_info")
+        return {"cluster": int(c[0]), "teams": int(t[0]), "smem_bytes": int(s[0]), "launches": int(l[0])}
 
 
 def mg_propagate_noalloc(N, dq, minv, hbar, pot_kind, pot_params, d_psi, q, p, n_steps, dt, scheme="strang",

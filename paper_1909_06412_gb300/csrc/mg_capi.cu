@@ -3,6 +3,7 @@
 // wavepackets, composition coefficients) and kernel launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -15,8 +16,8 @@
 namespace mgk {
 void* propagate_kernel(int prec, int kind);
 void* obs_kernel(int prec, int kind);
-void* init_tables_kernel();
-void* obs_tables_kernel();
+void* init_tables_kernel(int prec);
+void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
 }  // namespace mgk
@@ -270,6 +271,7 @@ struct mg_ctx {
   size_t work_bytes;
   double q[MAXD], p[MAXD], t;
   bool pot_set, state_set;
+  bool tables_stale;  // the grid centre moved in a batched launch; A tables to rebuild
   int64_t launches;
   std::vector<double> host;  // staging for psi
   std::vector<double> gam;
@@ -301,8 +303,11 @@ mg_status launch_plain(mg_ctx* c, void* fn, void** args, size_t smem) {
 
 mg_status init_tables(mg_ctx* c) {
   void* args[] = {&c->P, &c->B};
-  return launch_plain(c, init_tables_kernel(), args, c->P.smem_bytes);
+  c->tables_stale = false;
+  return launch_plain(c, init_tables_kernel(c->P.prec), args, c->P.smem_bytes);
 }
+
+mg_status refresh_tables(mg_ctx* c) { return c->tables_stale ? init_tables(c) : MG_OK; }
 
 mg_status read_status(mg_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -624,6 +629,7 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
   if (!scheme_coeffs(scheme, c->gam)) return MG_ERR_ARG;
   if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
   if (n_steps == 0) return MG_OK;
+  if (refresh_tables(c) != MG_OK) return MG_ERR_CUDA;
   Run R{};
   R.n_steps = n_steps;
   R.S = (int)c->gam.size();
@@ -691,7 +697,8 @@ mg_status mg_get_observables(mg_ctx* c, double* norm, double* energy, double* me
   if (s != MG_OK) return s;
   const Plan& P = c->P;
   void* targs[] = {&c->P, &c->B};
-  s = launch_plain(c, obs_tables_kernel(), targs, P.smem_bytes);
+  s = refresh_tables(c);
+  if (s == MG_OK) s = launch_plain(c, obs_tables_kernel(P.prec), targs, P.smem_bytes);
   void* fn = obs_kernel(P.prec, P.pot_kind);
   for (int l = P.D - 1; l >= 0 && s == MG_OK; --l) {
     int mode = 0;
@@ -1061,9 +1068,9 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   // ---- launches: A tables for the starting p-centre, then the propagation ----
   void* targs[] = {&P, &B};
   if (P.smem_bytes > 48 * 1024 &&
-      cudaFuncSetAttribute(init_tables_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes) != cudaSuccess)
+      cudaFuncSetAttribute(init_tables_kernel(P.prec), cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes) != cudaSuccess)
     return MG_ERR_CUDA;
-  if (cudaLaunchKernel(init_tables_kernel(), dim3(P.nblocks), dim3(THREADS), targs, P.smem_bytes, st) != cudaSuccess)
+  if (cudaLaunchKernel(init_tables_kernel(P.prec), dim3(P.nblocks), dim3(THREADS), targs, P.smem_bytes, st) != cudaSuccess)
     return MG_ERR_CUDA;
   Run R;
   std::memset(&R, 0, sizeof(Run));
@@ -1091,3 +1098,393 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   }
   return MG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched propagation: many grid contexts advanced by one persistent launch
+// of thread-block clusters, replayed from a CUDA graph.
+// ---------------------------------------------------------------------------
+
+namespace mgk {
+void* batch_kernel(int prec);
+}
+
+namespace {
+
+constexpr int BATCH_MAXD = 3;
+constexpr int BATCH_SMEM_CAP = 227 * 1024;
+
+// Must match batch_carve() in mg_batch.cu.
+size_t batch_smem_bytes(const BatchArgs& A, int prec) {
+  const size_t vs = prec == 0 ? sizeof(double2) : sizeof(float2);
+  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t TT = (size_t)A.tab_total;
+  return 4 * r16(vs * TT) + r16(sizeof(double) * NVCOL * TT) + r16(sizeof(double) * TT) +
+         r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (A.D + 2)) + r16(sizeof(double) * PSTRIDE) +
+         r16(sizeof(double) * SCALARS) + 3 * r16((size_t)A.region_bytes) + r16(sizeof(uint64_t) * 3) +
+         r16(sizeof(unsigned) * 4) + r16(sizeof(int64_t) * A.max_tiles) +
+         r16(sizeof(uint16_t) * A.max_lines * A.D);
+}
+
+// Tiles of one problem for a team of C CTAs: on each axis W lines per tile,
+// the largest power of two whose tile stays within `target` bytes (at least
+// 16-byte rows on strided axes, for the bulk copies).  Returns the largest
+// tile in bytes.
+int64_t batch_tiles(Plan& P, int C, int64_t target) {
+  const int64_t vs = P.prec == 0 ? 16 : 8;
+  int64_t big = 0;
+  P.nblocks = C;
+  P.resident = 0;
+  for (int l = 0; l < P.D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    const bool contig = (l == P.D - 1);
+    const int64_t lines = P.npts / ax.n;
+    const int64_t lim = std::max<int64_t>(1, target / ((int64_t)ax.n * vs));
+    const int64_t mult = contig ? lines : ax.stride;
+    int64_t W = 1;
+    while (W * 2 <= lim && mult % (W * 2) == 0) W *= 2;
+    if (!contig && W * vs < 16) W = std::min<int64_t>(ax.stride, 16 / vs);
+    ax.W = (int)W;
+    ax.ntiles = lines / W;
+    big = std::max<int64_t>(big, W * ax.n * vs);
+  }
+  return big;
+}
+
+// Chunks and radix plans of one problem once the region size is known.
+void batch_chunks(Plan& P, int64_t region, int rmax_req, int& max_tiles, int& max_lines) {
+  const int64_t vs = P.prec == 0 ? 16 : 8;
+  for (int l = 0; l < P.D; ++l) {
+    AxisPlan& ax = P.ax[l];
+    const int64_t tile = (int64_t)ax.W * ax.n * vs;
+    ax.tpc = (int)std::max<int64_t>(1, region / tile);
+    const int64_t mine = std::max<int64_t>(1, (ax.ntiles + P.nblocks - 1) / P.nblocks);
+    const int64_t tiles = std::min<int64_t>(mine, ax.tpc);
+    const int64_t lines = tiles * ax.W;
+    const int rmax = rmax_req ? rmax_req : (lines * ax.n / 8 >= 128 ? 8 : (lines * ax.n / 4 >= 128 ? 4 : 2));
+    radix_plan(ax.n, ax, rmax);
+    max_tiles = (int)std::max<int64_t>(max_tiles, tiles);
+    max_lines = (int)std::max<int64_t>(max_lines, lines);
+  }
+}
+
+// Relative cost of one stage of a problem (transform work per point grows
+// with the log of the axis lengths; the multipliers and reductions add a
+// per-point constant).
+double batch_cost(const Plan& P) {
+  double lg = 0;
+  for (int l = 0; l < P.D; ++l) lg += std::log2((double)P.ax[l].n);
+  return (double)P.npts * (lg + 2.0 * P.D + 4.0);
+}
+
+struct BatchLayout {
+  size_t probs, team_start, team_items, run, bstatus, sct, total;
+};
+
+BatchLayout batch_layout(int nprob) {
+  BatchLayout L{};
+  size_t o = 0;
+  auto put = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.probs = put((size_t)nprob * sizeof(BatchProb));
+  L.team_start = put((size_t)(MAXTEAMS + 1) * sizeof(int));
+  L.team_items = put((size_t)nprob * sizeof(int));
+  L.run = put(sizeof(BatchRun) + (size_t)nprob * sizeof(double));
+  L.bstatus = put((size_t)nprob * sizeof(int));
+  L.sct = put(256 * sizeof(double2));
+  L.total = o;
+  return L;
+}
+
+bool same_potential(const Plan& a, const Plan& b) {
+  return a.pot_kind == b.pot_kind && a.pot_general == b.pot_general &&
+         std::memcmp(a.pot, b.pot, sizeof(a.pot)) == 0;
+}
+
+}  // namespace
+
+struct mg_batch {
+  int nprob, prec, C, nteams, smem;
+  std::vector<mg_ctx*> ctx;
+  std::vector<BatchProb> hprob;
+  BatchLayout L;
+  BatchArgs A;
+  char* d_work;
+  cudaStream_t stream;  // the contexts' stream
+  cudaStream_t cap;     // private stream the launch was captured on
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  cudaEvent_t done;
+  bool pending;
+  unsigned char* h_run;  // pinned: BatchRun then one dt per problem
+  size_t run_bytes;
+  int64_t launches;
+};
+
+extern "C" {
+
+size_t mg_batch_workspace_bytes(int nprob) {
+  if (nprob < 1) return 0;
+  return batch_layout(nprob).total;
+}
+
+mg_status mg_batch_destroy(mg_batch* b) {
+  if (!b) return MG_ERR_ARG;
+  if (b->pending) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->h_run) cudaFreeHost(b->h_run);
+  delete b;
+  return MG_OK;
+}
+
+mg_status mg_batch_create(mg_batch** out, int nprob, mg_ctx* const* ctxs, int cluster, const int* tile_bytes,
+                          const int* radix_max, void* d_work, size_t work_bytes) {
+  if (!out || !ctxs || nprob < 1 || !d_work) return MG_ERR_ARG;
+  *out = nullptr;
+  if (cluster == 0) cluster = 2;
+  if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return MG_ERR_ARG;
+  if (((uintptr_t)d_work & 255)) return MG_ERR_ARG;
+  const BatchLayout L = batch_layout(nprob);
+  if (work_bytes < L.total) return MG_ERR_ARG;
+  const int prec = ctxs[0] ? ctxs[0]->P.prec : 0;
+  for (int i = 0; i < nprob; ++i) {
+    const mg_ctx* c = ctxs[i];
+    if (!c) return MG_ERR_ARG;
+    if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
+    if (c->P.prec != prec || c->stream != ctxs[0]->stream) return MG_ERR_ARG;
+    if (c->P.D > BATCH_MAXD) return MG_ERR_UNSUPPORTED;
+    if (tile_bytes && tile_bytes[i] < 0) return MG_ERR_ARG;
+    if (radix_max && radix_max[i] != 0 && radix_max[i] != 2 && radix_max[i] != 4 && radix_max[i] != 8)
+      return MG_ERR_ARG;
+  }
+  mg_batch* b = new mg_batch();
+  b->nprob = nprob;
+  b->prec = prec;
+  b->C = cluster;
+  b->L = L;
+  b->d_work = (char*)d_work;
+  b->stream = ctxs[0]->stream;
+  b->ctx.assign(ctxs, ctxs + nprob);
+  b->hprob.resize(nprob);
+  std::memset(b->hprob.data(), 0, sizeof(BatchProb) * nprob);
+
+  // ---- tiles, chunk region and shared-memory layout --------------------------
+  const int64_t def_target = prec == 0 ? 32768 : 16384;
+  int64_t scale_num = 1, scale_den = 1;  // shrinks every target while the layout is too large
+  BatchArgs& A = b->A;
+  std::memset(&A, 0, sizeof(BatchArgs));
+  for (;;) {
+    int64_t big = 0;
+    A.D = 1;
+    A.tab_total = 1;
+    for (int i = 0; i < nprob; ++i) {
+      Plan& P = b->hprob[i].P;
+      P = ctxs[i]->P;
+      const int64_t t = (tile_bytes && tile_bytes[i] ? tile_bytes[i] : def_target) * scale_num / scale_den;
+      big = std::max(big, batch_tiles(P, cluster, std::max<int64_t>(t, 1)));
+      A.D = std::max(A.D, P.D);
+      A.tab_total = std::max(A.tab_total, P.tab_total);
+    }
+    const int64_t region = ((std::max(big, def_target * scale_num / scale_den) + 15) / 16) * 16;
+    A.region_bytes = (int)region;
+    A.max_tiles = 1;
+    A.max_lines = 1;
+    for (int i = 0; i < nprob; ++i)
+      batch_chunks(b->hprob[i].P, region, radix_max ? radix_max[i] : 0, A.max_tiles, A.max_lines);
+    A.smem_bytes = (int)batch_smem_bytes(A, prec);
+    for (int i = 0; i < nprob; ++i) {
+      Plan& P = b->hprob[i].P;
+      P.region_bytes = A.region_bytes;
+      P.max_tiles = A.max_tiles;
+      P.max_lines = A.max_lines;
+      P.smem_bytes = A.smem_bytes;
+    }
+    if (A.smem_bytes <= BATCH_SMEM_CAP) break;
+    if (scale_den >= 64) {
+      delete b;
+      return MG_ERR_UNSUPPORTED;
+    }
+    scale_den *= 2;
+  }
+  b->smem = A.smem_bytes;
+
+  void* fn = batch_kernel(prec);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, A.smem_bytes) != cudaSuccess) {
+    delete b;
+    return MG_ERR_CUDA;
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = A.smem_bytes;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess || ncl < 1) {
+    delete b;
+    return MG_ERR_UNSUPPORTED;
+  }
+  b->nteams = std::min(std::min(ncl, nprob), MAXTEAMS);
+  A.nteams = b->nteams;
+
+  // ---- longest-processing-time assignment of problems to teams ----------------
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::vector<double> cost(nprob);
+  for (int i = 0; i < nprob; ++i) cost[i] = batch_cost(b->hprob[i].P);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<double> load(b->nteams, 0.0);
+  std::vector<std::vector<int>> lists(b->nteams);
+  for (int i : order) {
+    int best = 0;
+    for (int t = 1; t < b->nteams; ++t)
+      if (load[t] < load[best]) best = t;
+    load[best] += cost[i];
+    lists[best].push_back(i);
+  }
+  std::vector<int> start(b->nteams + 1, 0), items;
+  items.reserve(nprob);
+  for (int t = 0; t < b->nteams; ++t) {
+    start[t] = (int)items.size();
+    items.insert(items.end(), lists[t].begin(), lists[t].end());
+  }
+  start[b->nteams] = (int)items.size();
+
+  // ---- device descriptors ------------------------------------------------------
+  for (int i = 0; i < nprob; ++i) {
+    BatchProb& Q = b->hprob[i];
+    const mg_ctx* c = ctxs[i];
+    Q.psi = c->B.psi;
+    Q.ctrl = c->B.ctrl;
+    Q.status = c->B.status;
+    Q.tw = c->B.tw;
+    Q.tc = c->B.tabC;
+  }
+  char* w = b->d_work;
+  A.probs = (const BatchProb*)(w + L.probs);
+  A.team_start = (const int*)(w + L.team_start);
+  A.team_items = (const int*)(w + L.team_items);
+  A.run = (const BatchRun*)(w + L.run);
+  A.dt = (const double*)(w + L.run + sizeof(BatchRun));
+  A.bstatus = (int*)(w + L.bstatus);
+  A.sct = (const double2*)(w + L.sct);
+  std::vector<double> sct(512);
+  fill_sincos_table(sct.data());
+  b->run_bytes = sizeof(BatchRun) + (size_t)nprob * sizeof(double);
+  mg_status s = cuda_ok(cudaMemcpy(w + L.probs, b->hprob.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpy(w + L.team_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpy(w + L.team_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (s == MG_OK) s = cuda_ok(cudaMemset(w + L.bstatus, 0, (size_t)nprob * sizeof(int)));
+  if (s == MG_OK) s = cuda_ok(cudaMemcpy(w + L.sct, sct.data(), 512 * sizeof(double), cudaMemcpyHostToDevice));
+  if (s == MG_OK) s = cuda_ok(cudaHostAlloc((void**)&b->h_run, b->run_bytes, cudaHostAllocDefault));
+  if (s == MG_OK) std::memset(b->h_run, 0, b->run_bytes);
+  if (s == MG_OK) s = cuda_ok(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  if (s == MG_OK) s = cuda_ok(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+
+  // ---- the launch as a graph: upload of the run parameters, then the kernel ----
+  if (s == MG_OK) s = cuda_ok(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  if (s == MG_OK) {
+    cudaError_t e = cudaMemcpyAsync(w + L.run, b->h_run, b->run_bytes, cudaMemcpyHostToDevice, b->cap);
+    cfg.gridDim = dim3(b->nteams * cluster);
+    cfg.stream = b->cap;
+    void* args[] = {&A};
+    if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, fn, args);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &b->graph);
+    s = cuda_ok(e != cudaSuccess ? e : e2);
+  }
+  if (s == MG_OK) s = cuda_ok(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  if (s != MG_OK) {
+    mg_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_propagate(mg_batch* b, int64_t n_steps, const double* dt, const char* scheme, int split,
+                             int grid_motion) {
+  if (!b || !dt || n_steps < 0) return MG_ERR_ARG;
+  if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
+    return MG_ERR_ARG;
+  for (int i = 0; i < b->nprob; ++i)
+    if (!std::isfinite(dt[i])) return MG_ERR_ARG;
+  std::vector<double> gam;
+  if (!scheme_coeffs(scheme, gam) || (int)gam.size() > MAX_STAGES) return MG_ERR_ARG;
+  if (n_steps == 0) return MG_OK;
+  // potentials changed through the contexts since the last launch
+  bool dirty = false;
+  for (int i = 0; i < b->nprob; ++i) {
+    const mg_ctx* c = b->ctx[i];
+    if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
+    Plan& P = b->hprob[i].P;
+    if (!same_potential(P, c->P)) {
+      P.pot_kind = c->P.pot_kind;
+      P.pot_general = c->P.pot_general;
+      std::memcpy(P.pot, c->P.pot, sizeof(P.pot));
+      dirty = true;
+    }
+  }
+  if (b->pending) {
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return MG_ERR_CUDA;
+    b->pending = false;
+  }
+  if (dirty &&
+      cudaMemcpyAsync(b->d_work + b->L.probs, b->hprob.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess)
+    return MG_ERR_CUDA;
+  BatchRun* R = (BatchRun*)b->h_run;
+  R->n_steps = n_steps;
+  R->S = (int)gam.size();
+  R->split = split;
+  R->motion = grid_motion;
+  for (size_t k = 0; k < gam.size(); ++k) R->gamma[k] = gam[k];
+  std::memcpy(b->h_run + sizeof(BatchRun), dt, sizeof(double) * b->nprob);
+  if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return MG_ERR_CUDA;
+  if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return MG_ERR_CUDA;
+  b->pending = true;
+  b->launches++;
+  for (int i = 0; i < b->nprob; ++i) {
+    b->ctx[i]->t += (double)n_steps * dt[i];
+    b->ctx[i]->tables_stale = true;
+  }
+  return MG_OK;
+}
+
+mg_status mg_batch_sync(mg_batch* b, int* first_failed) {
+  if (!b) return MG_ERR_ARG;
+  if (first_failed) *first_failed = -1;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MG_ERR_CUDA;
+  b->pending = false;
+  std::vector<int> st(b->nprob);
+  if (cudaMemcpy(st.data(), b->d_work + b->L.bstatus, sizeof(int) * b->nprob, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MG_ERR_CUDA;
+  for (int i = 0; i < b->nprob; ++i)
+    if (st[i] != 0) {
+      if (first_failed) *first_failed = i;
+      cudaMemset(b->d_work + b->L.bstatus, 0, sizeof(int) * b->nprob);
+      return (mg_status)st[i];
+    }
+  return MG_OK;
+}
+
+mg_status mg_batch_info(const mg_batch* b, int* cluster, int* nteams, int* smem_bytes, int64_t* launches) {
+  if (!b) return MG_ERR_ARG;
+  if (cluster) *cluster = b->C;
+  if (nteams) *nteams = b->nteams;
+  if (smem_bytes) *smem_bytes = b->smem;
+  if (launches) *launches = b->launches;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -399,7 +399,7 @@ template <typename V> __device__ void load_tables(const Plan& P, const Bufs& B, 
 
 // Per-point evaluation from per-axis tables.  th = -sigma V / hbar (or V
 // itself when the tables were built with scale 1), g = grad V.
-template <int KIND>
+template <int KIND, int DM = MAXD>
 __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const int* idx, double sgh,
                                        double& th, double* g) {
   const int TT = P.tab_total;
@@ -409,23 +409,23 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
     if (!P.pot_general) {
       th = 0;
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a)
+      for (int a = 0; a < DM; ++a)
         if (a < D) {
           th += COL(0, a);
           g[a] = COL(1, a);
         }
     } else {
-      double d[MAXD];
+      double d[DM];
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a)
+      for (int a = 0; a < DM; ++a)
         if (a < D) d[a] = COL(0, a);
       double v = 0;
 #pragma unroll
-      for (int a = 0; a < MAXD; ++a)
+      for (int a = 0; a < DM; ++a)
         if (a < D) {
           double s = 0;
 #pragma unroll
-          for (int b = 0; b < MAXD; ++b)
+          for (int b = 0; b < DM; ++b)
             if (b < D) s += P.pot[a * D + b] * d[b];
           g[a] = s;
           v += d[a] * s;
@@ -440,10 +440,10 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
     g[1] = fma(gR, dh, df);
   } else if (KIND == POT_HENON_HEILES) {
     const double lam = P.pot[0];
-    double x[MAXD], x2[MAXD];
+    double x[DM], x2[DM];
     double s1 = 0, cpl = 0;
 #pragma unroll
-    for (int a = 0; a < MAXD; ++a)
+    for (int a = 0; a < DM; ++a)
       if (a < D) {
         x[a] = COL(0, a);
         x2[a] = COL(2, a);
@@ -451,7 +451,7 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
         g[a] = COL(3, a);
       }
 #pragma unroll
-    for (int a = 0; a + 1 < MAXD; ++a)
+    for (int a = 0; a + 1 < DM; ++a)
       if (a + 1 < D) {
         cpl = fma(x2[a], x[a + 1], cpl);
         g[a] = fma(2.0 * lam * x[a], x[a + 1], g[a]);
@@ -469,9 +469,9 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
 }
 
 // Potential columns of one table entry (axis a, coordinate x).
-__device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, double sgh) {
-  const int TT = P.tab_total;
-  double c[NVCOL] = {0, 0, 0, 0, 0};
+__device__ void vcolumns_eval(const Plan& P, int a, double x, double sgh, double* c) {
+#pragma unroll
+  for (int k = 0; k < NVCOL; ++k) c[k] = 0.0;
   if (P.pot_kind == POT_HARMONIC) {
     const double d = x - P.pot[P.D * P.D + a];
     if (!P.pot_general) {
@@ -514,6 +514,11 @@ __device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, d
       c[0] = exp(-al * x);
     }
   }
+}
+__device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, double sgh) {
+  const int TT = P.tab_total;
+  double c[NVCOL];
+  vcolumns_eval(P, a, x, sgh, c);
 #pragma unroll
   for (int k = 0; k < NVCOL; ++k) __stcg(B.tabV + k * TT + e, c[k]);
 }
@@ -566,6 +571,34 @@ __device__ double2 round_unit_f32(double x, double y, double m2) {
 // so that they run on as many SM sub-partitions as possible at once.  Inputs
 // (tau, delta, p, q, sgh) come from the CTA's scalar slots.  A grid barrier
 // must follow before the tables are used.
+// Table entries of axis a, index j (c = j - N_a/2), from the CTA's scalars.
+// Kinetic factor K_a[j] = e^{(i/hbar)(delta_a p^K - tau minv_a (p^K)^2 / 2)}.
+__device__ __forceinline__ double2 kin_entry(const Plan& P, const double* sc, const double2* sct, int a, double c) {
+  const double pk = fma(c, P.dp[a], sc[SC_P + a]);
+  const double th = (sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk) / P.hbar;
+  double sn, cs;
+  expi_prec(P.prec, th, sct, sn, cs);
+  return P.prec ? round_unit_f32(cs, sn, 1.0) : make_double2(cs, sn);
+}
+// Demodulation A_a[j] = (-1)^j e^{-i p_a c dq_a / hbar} and conj(A_a[j]) / N_a.
+__device__ __forceinline__ void demod_entry(const Plan& P, const double* sc, const double2* sct, int a, int j,
+                                            double c, double2& A, double2& Ai) {
+  const int n = P.ax[a].n;
+  const double th = -sc[SC_P + a] * c * P.dq[a] / P.hbar;
+  double sn, cs;
+  expi_prec(P.prec, th, sct, sn, cs);
+  const double sg = (j & 1) ? -1.0 : 1.0;
+  // conj(A)/N by division: a rounded 1/N would bias every inverse transform
+  if (P.prec) {
+    A = round_unit_f32(sg * cs, sg * sn, 1.0);
+    const double inv = 1.0 / ((double)n * (double)n);
+    Ai = round_unit_f32(sg * cs / (double)n, -sg * sn / (double)n, inv);
+  } else {
+    A = make_double2(sg * cs, sg * sn);
+    Ai = make_double2(sg * cs / (double)n, -sg * sn / (double)n);
+  }
+}
+
 template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
   const int TT = P.tab_total, D = P.D;
   const int nch = (TT + 31) / 32;
@@ -587,30 +620,54 @@ template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B,
     const double c = (double)(j - n / 2);
     const double* sc = S.sc;
     if (kind == TB_K) {
-      const double pk = fma(c, P.dp[a], sc[SC_P + a]);
-      const double th = (sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk) / P.hbar;
-      double sn, cs;
-      expi_prec(P.prec, th, S.sct, sn, cs);
-      __stcg(B.tabK + e, P.prec ? round_unit_f32(cs, sn, 1.0) : make_double2(cs, sn));
+      __stcg(B.tabK + e, kin_entry(P, sc, S.sct, a, c));
     } else if (kind == TB_A) {
-      const double th = -sc[SC_P + a] * c * P.dq[a] / P.hbar;
-      double sn, cs;
-      expi_prec(P.prec, th, S.sct, sn, cs);
-      const double sg = (j & 1) ? -1.0 : 1.0;
-      // conj(A)/N by division: a rounded 1/N would bias every inverse transform
-      if (P.prec) {
-        __stcg(B.tabA + e, round_unit_f32(sg * cs, sg * sn, 1.0));
-        const double inv = 1.0 / ((double)n * (double)n);
-        __stcg(B.tabAi + e, round_unit_f32(sg * cs / (double)n, -sg * sn / (double)n, inv));
-      } else {
-        __stcg(B.tabA + e, make_double2(sg * cs, sg * sn));
-        __stcg(B.tabAi + e, make_double2(sg * cs / (double)n, -sg * sn / (double)n));
-      }
+      double2 A, Ai;
+      demod_entry(P, sc, S.sct, a, j, c, A, Ai);
+      __stcg(B.tabA + e, A);
+      __stcg(B.tabAi + e, Ai);
     } else if (kind == TB_V) {
       vcolumns(P, B, e, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH]);
     } else {
       const double pk = fma(c, P.dp[a], sc[SC_P + a]);
       __stcg(B.tabE + e, 0.5 * P.minv[a] * pk * pk);
+    }
+  }
+}
+
+// The same tables built by one CTA for itself, straight into its shared
+// memory (grids small enough for a few CTAs; no barrier needed across CTAs).
+// Tasks of 32 entries are dealt out over the CTA's warps.
+template <typename V> __device__ void build_tables_local(const Plan& P, const Smem<V>& S, int what) {
+  const int TT = P.tab_total, D = P.D;
+  const int nch = (TT + 31) / 32;
+  int kinds[3], nk = 0;
+  if (what & TB_K) kinds[nk++] = TB_K;
+  if (what & TB_V) kinds[nk++] = TB_V;
+  if (what & TB_A) kinds[nk++] = TB_A;
+  const int ntask = nk * nch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int t = warp; t < ntask; t += nwarps) {
+    const int kind = kinds[t / nch];
+    const int e = (t % nch) * 32 + lane;
+    if (e >= TT) continue;
+    int a = 0;
+    while (a + 1 < D && e >= P.ax[a + 1].toff) ++a;
+    const int j = e - P.ax[a].toff;
+    const double c = (double)(j - P.ax[a].n / 2);
+    const double* sc = S.sc;
+    if (kind == TB_K) {
+      S.tK[e] = from_d2<V>(kin_entry(P, sc, S.sct, a, c));
+    } else if (kind == TB_A) {
+      double2 A, Ai;
+      demod_entry(P, sc, S.sct, a, j, c, A, Ai);
+      S.tA[e] = from_d2<V>(A);
+      S.tAi[e] = from_d2<V>(Ai);
+    } else {
+      double cv[NVCOL];
+      vcolumns_eval(P, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH], cv);
+#pragma unroll
+      for (int k = 0; k < NVCOL; ++k) S.tv[k * TT + e] = cv[k];
     }
   }
 }
@@ -629,18 +686,24 @@ __device__ __forceinline__ double warp_sum(double x) {
 // through shared memory so that warp v sums value v (8 partials per lane, then
 // a shuffle tree): nv short FP64 chains on different sub-partitions instead of
 // nv * 8 warps of shuffle trees.
-template <typename V>
-__device__ void block_partials(const Bufs& B, const Smem<V>& S, int slot, const double* acc, int nv) {
+// The record goes to `rec` (shared memory, read by the other CTAs of a
+// cluster) or, when rec is null, to the grid's per-CTA slot in global memory.
+template <typename V, int DM = MAXD>
+__device__ void block_partials(const Bufs& B, const Smem<V>& S, int slot, const double* acc, int nv,
+                               double* rec = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nt = blockDim.x;
 #pragma unroll
-  for (int v = 0; v < MAXD + 2; ++v)
+  for (int v = 0; v < DM + 2; ++v)
     if (v < nv) S.red[v * nt + threadIdx.x] = acc[v];
   __syncthreads();
   for (int v = warp; v < nv; v += nt >> 5) {
     double s = 0;
     for (int k = lane; k < nt; k += 32) s += S.red[v * nt + k];
     s = warp_sum(s);
-    if (lane == 0) __stcg(B.part + ((size_t)slot * gridDim.x + blockIdx.x) * PSTRIDE + v, s);
+    if (lane == 0) {
+      if (rec) rec[v] = s;
+      else __stcg(B.part + ((size_t)slot * gridDim.x + blockIdx.x) * PSTRIDE + v, s);
+    }
   }
   __syncthreads();
 }
@@ -675,6 +738,10 @@ struct PassArgs {
   int slot;       // partial-sum slot
   const void* src;
   void* dst;
+  // position in the team of CTAs sharing the grid (default: the whole launch)
+  // and, for teams smaller than the launch, the shared-memory reduction record
+  int64_t bid = 0, nb = 0;
+  double* rec = nullptr;
 };
 
 // s + c += x with Knuth's error-free two-sum (FP32).
@@ -706,11 +773,10 @@ __device__ __forceinline__ void decode(const Plan& P, int l, unsigned o, unsigne
 // one line of n elements (one copy).
 template <typename V>
 __device__ void issue_chunk(const AxisPlan& ax, bool contig, const V* src, int64_t c0, int nt, V* reg,
-                            uint64_t* bar) {
+                            uint64_t* bar, int64_t bid, int64_t nb) {
   const int lane = threadIdx.x & 31;
   const int n = ax.n, W = ax.W;
   const int64_t s = ax.stride, tpo = contig ? 1 : ax.stride / W;
-  const int64_t bid = blockIdx.x, nb = gridDim.x;
   const unsigned rowbytes = (unsigned)((contig ? W * n : W) * sizeof(V));
   const int rows = contig ? nt : nt * n;
   fence_proxy_async();  // earlier generic accesses to `reg` before the async writes
@@ -741,7 +807,7 @@ __device__ __forceinline__ void wait_region(const Bufs& B, uint64_t* bar, unsign
   }
 }
 
-template <typename T, bool INV, int KIND>
+template <typename T, bool INV, int KIND, int DM = MAXD>
 __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const Smem<typename VT<T>::v>& S,
                          int res_in) {
   using V = typename VT<T>::v;
@@ -758,17 +824,17 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   const V* post = A.post ? S.tAi + ax.toff : nullptr;
   const double sgh = S.sc[SC_SGH];
 
-  double acc[MAXD + 2];
+  double acc[DM + 2];
 #pragma unroll
-  for (int v = 0; v < MAXD + 2; ++v) acc[v] = 0;
+  for (int v = 0; v < DM + 2; ++v) acc[v] = 0;
   // FP32 storage: the kinetic moments are summed per thread in FP32 with an
   // error-free two-sum (sum + compensation), so the per-thread partials are
   // accurate to ~1e-14 without an FP64 instruction per point.
-  float ks[MAXD + 1], kc[MAXD + 1];
+  float ks[DM + 1], kc[DM + 1];
 #pragma unroll
-  for (int v = 0; v < MAXD + 1; ++v) ks[v] = kc[v] = 0.f;
+  for (int v = 0; v < DM + 1; ++v) ks[v] = kc[v] = 0.f;
 
-  const int64_t bid = blockIdx.x, nb = gridDim.x;
+  const int64_t bid = A.nb ? A.bid : (int64_t)blockIdx.x, nb = A.nb ? A.nb : (int64_t)gridDim.x;
   const int64_t mine = bid < ax.ntiles ? (ax.ntiles - bid + nb - 1) / nb : 0;
   const V* src = (const V*)A.src;
   V* dst = (V*)A.dst;
@@ -781,14 +847,16 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
   unsigned parity = 0;          // one phase bit per region
   if (stream) {
     parity = *S.mphase;
-    if (threadIdx.x < 32) issue_chunk(ax, contig, src, 0, (int)(mine < chunk ? mine : chunk), S.reg[rd], S.mbar + rd);
+    if (threadIdx.x < 32)
+      issue_chunk(ax, contig, src, 0, (int)(mine < chunk ? mine : chunk), S.reg[rd], S.mbar + rd, bid, nb);
   }
   for (int64_t c0 = 0; c0 < mine; c0 += chunk) {
     const int nt = (int)(mine - c0 < chunk ? mine - c0 : chunk);
     const int cnt = nt * W * n;
     if (stream && c0 + chunk < mine && threadIdx.x < 32) {
       const int64_t c1 = c0 + chunk;
-      issue_chunk(ax, contig, src, c1, (int)(mine - c1 < chunk ? mine - c1 : chunk), S.reg[rf], S.mbar + rf);
+      issue_chunk(ax, contig, src, c1, (int)(mine - c1 < chunk ? mine - c1 : chunk), S.reg[rf], S.mbar + rf, bid,
+                  nb);
     }
     // per-tile offsets (one 64-bit division per tile, not per element) and,
     // for the fused reductions, the multi-index of every line of the chunk
@@ -802,7 +870,7 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
         const int k = kw / W, w = kw - k * W;
         const int64_t t = bid + (c0 + k) * nb;
         const int64_t o = t / tpo;
-        int idx[MAXD];
+        int idx[DM];
         const unsigned lo = contig ? (unsigned)(t * W + w) : (unsigned)o;
         const unsigned li = contig ? 0u : (unsigned)((t - o * tpo) * W + w);
         decode(P, A.l, lo, li, 0, idx);
@@ -866,9 +934,9 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
       V v = cur[e];
       if (post) v = cmul(v, post[j]);
       if (A.red != RED_NONE) {
-        int idx[MAXD];
+        int idx[DM];
 #pragma unroll
-        for (int a = 0; a < MAXD; ++a)
+        for (int a = 0; a < DM; ++a)
           if (a < D) idx[a] = S.li[(ti * W + w) * D + a];
         idx[A.l] = j;
         // |value|^2: FP64 for FP64 storage; FP32 product, FP64 accumulation otherwise
@@ -878,7 +946,7 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
             const float w2f = fmaf(v.x, v.x, v.y * v.y);
             two_sum_acc(ks[0], kc[0], w2f);
 #pragma unroll
-            for (int a = 0; a < MAXD; ++a)
+            for (int a = 0; a < DM; ++a)
               if (a < D) two_sum_acc(ks[1 + a], kc[1 + a], (float)(idx[a] - (P.ax[a].n >> 1)) * w2f);
             handled = true;
           }
@@ -891,18 +959,18 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
           if (A.red == RED_KIN || A.red == RED_OBS_KIN) {
             double te = 0;
 #pragma unroll
-            for (int a = 0; a < MAXD; ++a)
+            for (int a = 0; a < DM; ++a)
               if (a < D) {
                 acc[1 + a] = fma(S.tc[P.ax[a].toff + idx[a]], w2, acc[1 + a]);
                 if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
               }
             if (A.red == RED_OBS_KIN) acc[D + 1] = fma(te, w2, acc[D + 1]);
           } else {
-            double th, g[MAXD];
-            vpoint<KIND>(P, S.tv, idx, sgh, th, g);
+            double th, g[DM];
+            vpoint<KIND, DM>(P, S.tv, idx, sgh, th, g);
             if (A.red == RED_V) {
 #pragma unroll
-              for (int a = 0; a < MAXD; ++a)
+              for (int a = 0; a < DM; ++a)
                 if (a < D) acc[1 + a] = fma(g[a], w2, acc[1 + a]);
               if constexpr (sizeof(T) == 8) {
                 double sn, cs;
@@ -920,7 +988,7 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
               }
             } else {  // observables: <x> and <V>
 #pragma unroll
-              for (int a = 0; a < MAXD; ++a)
+              for (int a = 0; a < DM; ++a)
                 if (a < D)
                   acc[1 + a] = fma(fma(S.tc[P.ax[a].toff + idx[a]], P.dq[a], S.sc[SC_Q + a]), w2, acc[1 + a]);
               acc[D + 1] = fma(th, w2, acc[D + 1]);
@@ -949,11 +1017,11 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
     if constexpr (sizeof(T) == 4) {
       if (A.red == RED_KIN) {
 #pragma unroll
-        for (int v = 0; v < MAXD + 1; ++v) acc[v] = (double)ks[v] + (double)kc[v];
+        for (int v = 0; v < DM + 1; ++v) acc[v] = (double)ks[v] + (double)kc[v];
       }
     }
     const int nv = (A.red == RED_OBS_KIN || A.red == RED_OBS_V) ? D + 2 : D + 1;
-    block_partials(B, S, A.slot, acc, nv);
+    block_partials<V, DM>(B, S, A.slot, acc, nv, A.rec ? A.rec + A.slot * PSTRIDE : nullptr);
   }
   return res;
 }

@@ -159,11 +159,13 @@ done:
   }
 }
 
-// Tables A/Ainv for the current p-centre (after a state upload).
+// Tables A/Ainv for the current p-centre (after a state upload).  The
+// shared-memory layout is the plan's own (element type of its precision).
+template <typename T>
 __global__ void __launch_bounds__(THREADS) k_init_tables(const __grid_constant__ Plan P,
                                                           const __grid_constant__ Bufs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<double2> S = carve<double2>(P, smem_raw);
+  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x < P.D) {
@@ -176,10 +178,11 @@ __global__ void __launch_bounds__(THREADS) k_init_tables(const __grid_constant__
 }
 
 // Observables: tables of V (unscaled) and of the kinetic energy.
+template <typename T>
 __global__ void __launch_bounds__(THREADS) k_obs_tables(const __grid_constant__ Plan P,
                                                          const __grid_constant__ Bufs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<double2> S = carve<double2>(P, smem_raw);
+  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x < P.D) {
@@ -285,8 +288,8 @@ void* obs_kernel(int prec, int kind) {
   return nullptr;
 }
 
-void* init_tables_kernel() { return (void*)k_init_tables; }
+void* init_tables_kernel(int prec) { return prec ? (void*)k_init_tables<float> : (void*)k_init_tables<double>; }
 void* set_product_kernel(int prec) { return prec ? (void*)k_set_product<float> : (void*)k_set_product<double>; }
-void* obs_tables_kernel() { return (void*)k_obs_tables; }
+void* obs_tables_kernel(int prec) { return prec ? (void*)k_obs_tables<float> : (void*)k_obs_tables<double>; }
 
 }  // namespace mgk

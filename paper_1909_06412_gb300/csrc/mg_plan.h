@@ -1,5 +1,5 @@
 // Plain-old-data descriptors shared by the host planner (mg_capi.cu) and the
-// device kernels (mg_kernels.cu).  No CUDA types beyond double2.
+// device kernels.  No CUDA types beyond double2.
 #pragma once
 #include <stdint.h>
 #include <vector_types.h>
@@ -87,6 +87,41 @@ struct AdjRun {
   void* ubar;            // device complex128 cotangent of psi (in: at t_end; out: at t_start)
   int ntheta;            // potential parameters differentiated (4 for atom-diatom)
   double norm;           // sum |u|^2, an invariant of the propagation
+};
+
+// ---- batched launch: many independent grids, one cluster of CTAs per grid ----
+
+constexpr int MAXTEAMS = 4096;  // clusters of one batched launch
+
+// One problem of a batch: its plan tiled for a team of CTAs, and the buffers
+// of the grid context that owns it.
+struct BatchProb {
+  Plan P;
+  void* psi;
+  double* ctrl;
+  int* status;
+  const double2* tw;
+  const double* tc;
+};
+
+// Parameters of one batched propagation (uploaded by the launch itself).
+struct BatchRun {
+  int64_t n_steps;
+  int S, split, motion, pad;
+  double gamma[MAX_STAGES];
+};
+
+struct BatchArgs {
+  const BatchProb* probs;
+  const int* team_start;   // [nteams + 1] offsets into team_items
+  const int* team_items;   // problem indices, each team's in processing order
+  const BatchRun* run;
+  const double* dt;        // per problem
+  int* bstatus;            // per problem: 0 or the failure status
+  const double2* sct;      // 256 entries e^{i k pi / 128}
+  int nteams;
+  // shared-memory layout (maxima over the problems)
+  int D, tab_total, region_bytes, max_tiles, max_lines, smem_bytes;
 };
 
 }  // namespace mgk

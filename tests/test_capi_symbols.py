@@ -71,3 +71,22 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     fake = ctypes.c_void_p(256)
     assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(bad), 1.0, 0, fake, fake, 1 << 30, None) == -2
     assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(minv), -1.0, 0, fake, fake, 1 << 30, None) == -1
+
+
+def test_batch_host_checks(lib):
+    import ctypes
+
+    lib.mg_batch_workspace_bytes.argtypes = [ctypes.c_int]
+    lib.mg_batch_workspace_bytes.restype = ctypes.c_size_t
+    assert lib.mg_batch_workspace_bytes(0) == 0
+    assert lib.mg_batch_workspace_bytes(512) > lib.mg_batch_workspace_bytes(1) > 0
+    lib.mg_batch_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    lib.mg_batch_create.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    # no contexts / no workspace: rejected before any device call
+    assert lib.mg_batch_create(ctypes.byref(out), 1, None, 0, None, None, None, 0) == -1
+    assert lib.mg_batch_create(None, 1, None, 0, None, None, None, 0) == -1
+    lib.mg_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.mg_batch_destroy.restype = ctypes.c_int
+    assert lib.mg_batch_destroy(None) == -1
