@@ -41,8 +41,11 @@ ADJ_STEPS = 200
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM bytes (read + write) of one propagate launch, from an ncu capture of
-# `python bench.py --profile`; valid only for the kernel source it was taken on.
-TRAFFIC_RECORD = {"kernel_sha256": None, "bytes_per_launch": None}
+# `python bench.py --profile`; valid only for the kernel sources it was taken on
+# (sha256 of mg_kernels.cu + mg_device.cuh + mg_plan.h, concatenated).
+TRAFFIC_RECORD = {"kernel_sha256": "d1f8b4b51577f4594ba9d0b27192edf7667f000d07d3e72a5c3f2a6a2258e36f",
+                  "bytes_per_launch": 1.327616e6 + 0.151040e6}
+KERNEL_SOURCES = ("mg_kernels.cu", "mg_device.cuh", "mg_plan.h")
 
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -68,8 +71,10 @@ def initial(mgmod):
 def traffic_per_launch():
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1909_06412_gb300", "csrc", "mg_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1909_06412_gb300", "csrc", f), "rb").read())
+    h = h.hexdigest()
     return TRAFFIC_RECORD["bytes_per_launch"] if h == TRAFFIC_RECORD["kernel_sha256"] else None
 
 
@@ -213,20 +218,39 @@ def cpu_baseline_and_error(mgmod, torch):
     return cpu, err
 
 
+def hh_propagator(mgmod, n, D, prec, dev=None):
+    """Henon-Heiles (lambda = 0.111803) on an n^D grid with balanced windows
+    (dq = sqrt(2 pi / n)), Gaussians at q = 2 with unit width."""
+    dq = math.sqrt(2 * math.pi / n)
+    g = mgmod.Propagator((n,) * D, (dq,) * D, precision=prec, device=dev)
+    g.set_potential(mgmod.MG_POT_HENON_HEILES, [0.111803])
+    g.set_separable([("gauss", 2.0, 0.0, 1.0)] * D, [2.0] * D, [0.0] * D)
+    return g
+
+
 def run_profile(args):
-    """The timed launches of the workload alone, for profiler captures: the
-    propagate kernel is launched warmup + steps times, STEPS_PER_CALL steps each."""
+    """The timed launches of a workload alone, for profiler captures: the
+    propagate kernel is launched warmup + steps times.  --profile-case
+    atom_diatom (default): the bench workload, STEPS_PER_CALL steps per call;
+    hh7_fp32 / hh7_fp64: Henon-Heiles on 16^7 (FP32) / 12^7 (FP64) grids,
+    suzuki4, one time step (5 TVT stages) per call."""
     import torch
     import paper_1909_06412_gb300 as mg
 
-    fac, qc, pc = initial(mg)
-    g = mg.Propagator(N_GRID, DQ, minv=MINV)
-    g.set_potential(mg.MG_POT_ATOM_DIATOM, POT)
-    g.set_separable(fac, qc, pc)
+    if args.profile_case == "atom_diatom":
+        fac, qc, pc = initial(mg)
+        g = mg.Propagator(N_GRID, DQ, minv=MINV)
+        g.set_potential(mg.MG_POT_ATOM_DIATOM, POT)
+        g.set_separable(fac, qc, pc)
+        call = lambda: g.propagate(STEPS_PER_CALL, DT, SCHEME)
+    else:
+        n, D, prec = {"hh7_fp32": (16, 7, mg.MG_FP32_MIXED), "hh7_fp64": (12, 7, mg.MG_FP64)}[args.profile_case]
+        g = hh_propagator(mg, n, D, prec)
+        call = lambda: g.propagate(1, 0.01, "suzuki4")
     for _ in range(args.warmup + args.steps):
-        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+        call()
     g.sync()
-    print(json.dumps({"profile_run": True, "launches": g.launches}))
+    print(json.dumps({"profile_run": True, "case": args.profile_case, "launches": g.launches}))
 
 
 def other_workloads(mgmod, torch, dev, flush):
@@ -376,6 +400,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed propagate calls, as in the timed region (for ncu captures)")
+    ap.add_argument("--profile-case", default="atom_diatom", choices=["atom_diatom", "hh7_fp32", "hh7_fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
