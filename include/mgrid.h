@@ -145,6 +145,16 @@ mg_status mg_adjoint(mg_ctx* ctx, int64_t n_steps, double dt, const char* scheme
 /* Number of kernels this context has launched so far. */
 int64_t mg_kernel_launches(const mg_ctx* ctx);
 
+/* Which propagation kernel mg_propagate uses for this context with its
+ * current potential: 1 = the short-axis kernel (D >= 3 axes, all of one
+ * length 8, 12 or 16, and a Henon-Heiles or diagonal harmonic potential:
+ * several axes transformed per pass over the state), 0 = the general kernel
+ * (one pass per axis), -1 for a NULL context or no potential yet.  The same
+ * method either way (Sec. II.G); only the memory traffic differs.  Setting
+ * the environment variable MG_SHORT_AXES=0 before mg_create turns the
+ * short-axis kernel off for that context. */
+int mg_propagate_path(const mg_ctx* ctx);
+
 /* <x> under the Morse ground state above (host quadrature helper for
  * choosing an initial grid centre). */
 double mg_morse_mean(double Dm, double a, double re, double mass, double hbar);

@@ -50,6 +50,8 @@ def lib():
         L.mg_sync.argtypes = [vp]
         L.mg_kernel_launches.argtypes = [vp]
         L.mg_kernel_launches.restype = i64
+        L.mg_propagate_path.argtypes = [vp]
+        L.mg_propagate_path.restype = i32
         L.mg_morse_mean.argtypes = [d, d, d, d, d]
         L.mg_morse_mean.restype = d
         L.mg_status_string.argtypes = [i32]
@@ -219,6 +221,11 @@ class Propagator:
     @property
     def launches(self):
         return int(lib().mg_kernel_launches(self._h))
+
+    @property
+    def path(self):
+        """1: mg_propagate runs the short-axis kernel, 0: the general one."""
+        return int(lib().mg_propagate_path(self._h))
 
 
 def mg_batch_workspace_bytes(nprob):

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mg_plan.h"
+#include "mg_short.h"
 #include "mgrid.h"
 
 namespace mgk {
@@ -20,6 +21,8 @@ void* init_tables_kernel(int prec);
 void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
+void* short_kernel(int prec, int n);
+int short_threads_for(int n);
 }  // namespace mgk
 
 using namespace mgk;
@@ -33,8 +36,19 @@ constexpr int CHUNK_REGION = 64 * 1024;  // bytes per smem region otherwise
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, scratch, total;
+  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, tabF, tabP, scratch, total;
 };
+
+// Axis length of a grid the short-axis kernel can take (D >= 3 axes, all of
+// one length 8, 12 or 16), else 0.
+int short_shape(int D, const int64_t* N) {
+  if (D < 3 || D > MAXD) return 0;
+  const int64_t n = N[0];
+  if (n != 8 && n != 12 && n != 16) return 0;
+  for (int l = 1; l < D; ++l)
+    if (N[l] != n) return 0;
+  return (int)n;
+}
 
 Layout layout_for(int D, const int64_t* N, int precision) {
   int64_t npts = 1, tt = 0;
@@ -63,6 +77,10 @@ Layout layout_for(int D, const int64_t* N, int precision) {
   L.tabE = put(tt * sizeof(double));
   L.gamma = put(MAX_STAGES * sizeof(double));
   L.sct = put(256 * sizeof(double2));
+  // per-axis and pair potential factors of the short-axis kernel
+  const int sn = short_shape(D, N);
+  L.tabF = put(sn ? tt * sizeof(double2) : 0);
+  L.tabP = put(sn ? (size_t)(D - 1) * sn * sn * sizeof(double2) : 0);
   L.scratch = put((size_t)npts * (precision == 0 ? sizeof(double2) : sizeof(float2)));
   L.total = o;
   return L;
@@ -186,6 +204,91 @@ void tile_plan(Plan& P) {
   }
 }
 
+// Groups, chunking and shared memory of the short-axis kernel (mg_short.h).
+// A chunk holds lpc lines along any axis of its group (one line per thread
+// for FP64, two for FP32).  The group that ends at the last axis takes the
+// most axes whose blocks tile a chunk; the other groups, from the back, the
+// most axes (up to SHORT_MAXG) whose chunk rows of WT adjacent elements are
+// at least 32 bytes (one DRAM sector) and divide the trailing index range.
+bool short_plan(const Plan& P, ShortPlan& SP) {
+  std::memset(&SP, 0, sizeof(ShortPlan));
+  const int D = P.D;
+  const int n = short_shape(D, P.N);
+  if (!n) return false;
+  const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
+  const int threads = short_threads_for(n);
+  const int lpc = threads * (P.prec == 0 ? 1 : 2);
+  auto pw = [&](int k) {
+    int64_t r = 1;
+    for (int i = 0; i < k; ++i) r *= n;
+    return r;
+  };
+  int gc = 0;
+  for (int g = 1; g <= std::min(D, SHORT_MAXG); ++g)
+    if (lpc % pw(g - 1) == 0) gc = g;
+  int ngr = 0;
+  {
+    GroupPlan& G = SP.grp[ngr++];
+    G.l0 = D - gc;
+    G.g = gc;
+    G.contig = 1;
+    G.WT = (int)(lpc / pw(gc - 1));
+    G.ng = (int)pw(gc);
+    G.inner = 1;
+    G.nb = 1;
+    G.nblk = P.npts / G.ng;
+    G.nchunks = (G.nblk + G.WT - 1) / G.WT;
+    G.PS = (int)(pw(gc - 1) * (n + 1) + (gc >= 2 ? 1 : 0));
+  }
+  for (int l1 = D - gc - 1; l1 >= 0;) {
+    bool ok = false;
+    for (int g = std::min(SHORT_MAXG, l1 + 1); g >= 1 && !ok; --g) {
+      if (lpc % pw(g - 1)) continue;
+      const int64_t W = lpc / pw(g - 1);
+      const int64_t inner = pw(D - 1 - l1);
+      if (inner % W) continue;
+      if (g > 1 && (size_t)W * vs < 32) continue;
+      GroupPlan& G = SP.grp[ngr++];
+      G.l0 = l1 - g + 1;
+      G.g = g;
+      G.contig = 0;
+      G.WT = (int)W;
+      G.ng = (int)pw(g);
+      G.inner = inner;
+      G.nb = inner / W;
+      G.nblk = 0;
+      G.nchunks = P.npts / ((int64_t)G.ng * inner) * G.nb;
+      G.PS = (int)(pw(g - 1) * (n + 1) + (g >= 2 ? 1 : 0));
+      l1 -= g;
+      ok = true;
+    }
+    if (!ok) return false;
+  }
+  SP.n = n;
+  SP.ngroups = ngr;
+  SP.threads = threads;
+  int re = 0;
+  for (int i = 0; i < ngr; ++i) re = std::max(re, SP.grp[i].WT * SP.grp[i].PS);
+  SP.region_elems = re;
+  // must match carve_short() in mg_short.cu
+  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t TT = (size_t)P.tab_total;
+  const size_t tabs = 5 * r16(vs * TT) + r16(sizeof(double2) * 256) + r16(sizeof(double) * 16 * 32) +
+                      r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) +
+                      r16(vs * (size_t)(D - 1) * n * n) + r16(ts * 5 * TT);
+  const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
+  for (int nreg = 3; nreg >= 2; --nreg) {
+    const size_t total = tabs + nreg * r16(vs * (size_t)re);
+    if (total <= cap) {
+      SP.nreg = nreg;
+      SP.smem_bytes = (int)total;
+      return true;
+    }
+  }
+  return false;
+}
+
 // ---- composition coefficients (eq:comp_TVT; Yoshida 1990 triple jump,
 // ---- Suzuki 1990 fractal), built by recursion on the order -----------------
 
@@ -264,6 +367,7 @@ double digamma(double x) {
 
 struct mg_ctx {
   Plan P;
+  ShortPlan SP;  // short-axis kernel plan (SP.on = 0 when the grid does not qualify)
   Bufs B;
   Layout L;
   cudaStream_t stream;
@@ -281,6 +385,12 @@ struct mg_ctx {
 namespace {
 
 mg_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? MG_OK : MG_ERR_CUDA; }
+
+// Potentials of the form sum_a f_a(x_a) + sum_a h_a(x_a) g_{a+1}(x_{a+1}),
+// the ones the short-axis kernel evaluates from per-axis and pair tables.
+bool uses_short_kernel(const Plan& P) {
+  return P.pot_kind == MG_POT_HENON_HEILES || (P.pot_kind == MG_POT_HARMONIC && !P.pot_general);
+}
 
 mg_status upload_ctrl(mg_ctx* c) {
   for (int a = 0; a < MAXD; ++a) {
@@ -449,6 +559,24 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
   B.gamma = (const double*)(w + L.gamma);
   B.sct = (double2*)(w + L.sct);
   B.scratch = (double2*)(w + L.scratch);
+
+  // short-axis kernel: one CTA per SM, all co-resident
+  const char* se = std::getenv("MG_SHORT_AXES");
+  if ((!se || std::atoi(se) != 0) && short_plan(P, c->SP)) {
+    void* fn = short_kernel(P.prec, c->SP.n);
+    int occ = 0;
+    if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->SP.smem_bytes) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->SP.threads, c->SP.smem_bytes) == cudaSuccess &&
+        occ >= 1) {
+      c->SP.nblocks = std::min(MAXBLOCKS, occ * sms);
+      c->SP.tabF = (double2*)(w + L.tabF);
+      c->SP.tabP = (double2*)(w + L.tabP);
+      c->SP.on = 1;
+    } else {
+      cudaGetLastError();
+      c->SP.on = 0;
+    }
+  }
 
   // static tables: twiddles e^{-2 pi i m/N_l} and k - N_l/2
   std::vector<double> tw(2 * P.tab_total), kc(P.tab_total);
@@ -642,6 +770,18 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
                                         cudaMemcpyHostToDevice, c->stream));
   if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
   if (s != MG_OK) return s;
+  if (c->SP.on && uses_short_kernel(c->P)) {
+    ShortPlan SP = c->SP;
+    SP.pairs = c->P.pot_kind == MG_POT_HENON_HEILES;
+    void* sfn = short_kernel(c->P.prec, SP.n);
+    void* sargs[] = {&c->P, &c->B, &R, &SP};
+    cudaError_t e = cudaLaunchCooperativeKernel(sfn, dim3(SP.nblocks), dim3(SP.threads), sargs, SP.smem_bytes,
+                                                c->stream);
+    c->launches++;
+    if (e != cudaSuccess) return MG_ERR_CUDA;
+    c->t += (double)n_steps * dt;
+    return MG_OK;
+  }
   void* fn = propagate_kernel(c->P.prec, c->P.pot_kind);
   if (!fn) return MG_ERR_UNSUPPORTED;
   if (c->P.smem_bytes > 48 * 1024 &&
@@ -811,6 +951,11 @@ mg_status mg_adjoint(mg_ctx* c, int64_t n_steps, double dt, const char* scheme, 
 }
 
 int64_t mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : -1; }
+
+int mg_propagate_path(const mg_ctx* c) {
+  if (!c || !c->pot_set) return -1;
+  return (c->SP.on && uses_short_kernel(c->P)) ? 1 : 0;
+}
 
 const char* mg_status_string(int s) {
   switch (s) {
