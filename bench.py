@@ -392,6 +392,104 @@ def adjoint_leg(mgmod, torch, dev):
     return out
 
 
+BATCH_STEPS = 200
+BATCH_SEPARATE_STEPS = 20
+
+
+def batch_problem_setup(mgmod, pr, precision):
+    """One problem of the seeded batch workload as a Propagator."""
+    g = mgmod.Propagator(pr["N"], pr["dq"], minv=1.0 / np.array(pr["mass"]), precision=precision)
+    if pr["kind"] == "atom_diatom":
+        Dm, a, re, A, be = pr["pot"]
+        g.set_potential(mgmod.MG_POT_ATOM_DIATOM, list(pr["pot"]))
+        R0, P0, sg = pr["gauss"][0]
+        mr = pr["mass"][1]
+        g.set_separable([("gauss", R0, P0, sg), ("morse", Dm, a, re, mr)],
+                        [R0, mgmod.mg_morse_mean(Dm, a, re, mr)], [P0, 0.0])
+    else:
+        k, c = pr["pot"]
+        D = len(k)
+        g.set_potential(mgmod.MG_POT_HARMONIC, list(np.diag(k).ravel()) + list(c))
+        g.set_separable([("gauss", q, p, sg) for q, p, sg in pr["gauss"]],
+                        [f[0] for f in pr["gauss"]], [f[1] for f in pr["gauss"]])
+    return g
+
+
+def batch_leg(mgmod, torch, dev):
+    """Batched serving-style launch on the seeded 512-grid workload (256 2D
+    grids of 64^2..256^2 points, harmonic or atom-diatom; 256 3D harmonic grids
+    of 16^3..48^3; parameters within +-20% of the 3D harmonic and atom-diatom
+    workloads): FP32 storage with FP64 reductions, suzuki4, one graph-replayed
+    batched launch of BATCH_STEPS steps, with the launch knobs from the
+    autotuner; against the same problems as 512 separate plain FP64
+    mg_propagate launches of BATCH_SEPARATE_STEPS steps each."""
+    import tempfile
+
+    from paper_1909_06412_gb300 import autotune
+    from tests import inputs
+
+    probs = inputs.batch_problems()
+    dts = np.array([pr["dt"] for pr in probs])
+    pts = np.array([int(np.prod(pr["N"])) for pr in probs])
+    gs = [batch_problem_setup(mgmod, pr, mgmod.MG_FP32_MIXED) for pr in probs]
+    cache = os.path.join(tempfile.mkdtemp(), "autotune.json")
+    t0 = time.perf_counter()
+    s, tb, rm, entry = autotune.tune_batch(gs, BATCH_STEPS, dts, "suzuki4", trial_steps=4, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    out = {"workload": "seeded 512-grid batch (2D 64^2-256^2, 3D 16^3-48^3), FP32 storage + FP64 reductions, "
+                       "suzuki4", "points": int(pts.sum()), "problems": len(probs),
+           "autotune": {"settings": s, "trials": entry["trials"], "tuning_s": tune_s,
+                        "trial_s_per_step_default": entry["default_seconds_per_step"],
+                        "trial_s_per_step_tuned": entry["seconds_per_step"]}}
+    for label, kw in (("default", {}), ("tuned", {"cluster": s["cluster"], "tile_bytes": tb, "radix_max": rm})):
+        b = mgmod.Batch(gs, **kw)
+        b.propagate(2, dts, "suzuki4")
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gs[0].stream)
+        b.propagate(BATCH_STEPS, dts, "suzuki4")
+        e1.record(gs[0].stream)
+        b.sync()
+        t = e0.elapsed_time(e1) / 1e3
+        out["batched_" + label] = {"value": float(pts.sum()) * BATCH_STEPS / t, "unit": UNIT, "s": t,
+                                   "steps": BATCH_STEPS, "launches": b.info()["launches"]}
+        b.close()
+    # error of the batched FP32 result against the FP64 single-grid path
+    # (itself pinned to the oracle), on every 64th problem after the runs above
+    errs = []
+    for i in range(0, len(probs), 64):
+        ref = batch_problem_setup(mgmod, probs[i], mgmod.MG_FP64)
+        ref.propagate(2 + BATCH_STEPS + 2 + BATCH_STEPS, dts[i], "suzuki4")
+        a, b2 = gs[i].get_state()[0], ref.get_state()[0]
+        errs.append(float(np.linalg.norm(a - b2) / np.linalg.norm(b2)))
+        ref.close()
+    out["batched_error_vs_fp64_single_grid"] = {"psi_rel_l2_max": max(errs), "problems_sampled": len(errs),
+                                                "steps": 2 * (BATCH_STEPS + 2)}
+    for g in gs:
+        g.close()
+    del gs
+    torch.cuda.empty_cache()
+    # 512 separate plain FP64 launches
+    gd = [batch_problem_setup(mgmod, pr, mgmod.MG_FP64) for pr in probs]
+    for g, dt in zip(gd, dts):
+        g.propagate(1, dt, "suzuki4")
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(gd[0].stream)
+    for g, dt in zip(gd, dts):
+        g.propagate(BATCH_SEPARATE_STEPS, dt, "suzuki4")
+    e1.record(gd[0].stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3
+    out["separate_fp64"] = {"value": float(pts.sum()) * BATCH_SEPARATE_STEPS / t, "unit": UNIT, "s": t,
+                            "steps": BATCH_SEPARATE_STEPS, "launches": len(gd)}
+    for g in gd:
+        g.close()
+    del gd
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,6 +586,7 @@ def main():
     mixed = mixed_precision_leg(mg, torch, dev, args, flush)
     others = other_workloads(mg, torch, dev, flush)
     adj = adjoint_leg(mg, torch, dev)
+    batch = batch_leg(mg, torch, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -515,6 +614,7 @@ def main():
         "mixed_precision": mixed,
         "other_workloads": others,
         "adjoint": adj,
+        "batch": batch,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,
