@@ -22,7 +22,8 @@ void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
 void* short_kernel(int prec, int n);
-int short_threads_for(int n);
+int short_threads_for(int prec, int n);
+int short_lpt_for(int prec, int n);
 }  // namespace mgk
 
 using namespace mgk;
@@ -36,7 +37,7 @@ constexpr int CHUNK_REGION = 64 * 1024;  // bytes per smem region otherwise
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, tabF, tabP, scratch, total;
+  size_t ctrl, bar, status, part, tw, tabA, tabAi, tabK, tabV, tabC, tabE, gamma, sct, tabF, tabP, tabB, scratch, total;
 };
 
 // Axis length of a grid the short-axis kernel can take (D >= 3 axes, all of
@@ -81,6 +82,7 @@ Layout layout_for(int D, const int64_t* N, int precision) {
   const int sn = short_shape(D, N);
   L.tabF = put(sn ? tt * sizeof(double2) : 0);
   L.tabP = put(sn ? (size_t)(D - 1) * sn * sn * sizeof(double2) : 0);
+  L.tabB = put(sn ? 2 * tt * sizeof(double2) : 0);
   L.scratch = put((size_t)npts * (precision == 0 ? sizeof(double2) : sizeof(float2)));
   L.total = o;
   return L;
@@ -217,8 +219,8 @@ bool short_plan(const Plan& P, ShortPlan& SP) {
   if (!n) return false;
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
-  const int threads = short_threads_for(n);
-  const int lpc = threads * (P.prec == 0 ? 1 : 2);
+  const int threads = short_threads_for(P.prec, n);
+  const int lpc = threads * short_lpt_for(P.prec, n);
   auto pw = [&](int k) {
     int64_t r = 1;
     for (int i = 0; i < k; ++i) r *= n;
@@ -571,6 +573,8 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
       c->SP.nblocks = std::min(MAXBLOCKS, occ * sms);
       c->SP.tabF = (double2*)(w + L.tabF);
       c->SP.tabP = (double2*)(w + L.tabP);
+      c->SP.tabB = (double2*)(w + L.tabB);
+      c->SP.tabC = c->SP.tabB + P.tab_total;
       c->SP.on = 1;
     } else {
       cudaGetLastError();

@@ -17,8 +17,15 @@
 //  - Each thread transforms whole lines held in registers: an n-point DFT of
 //    compile-time length (8: radix-8 codelet; 12 = 4 x 3 and 16 = 4 x 4 as two
 //    codelet stages with the twiddles in between).
-//  - The multipliers of the method are applied per line: A_l before the
-//    forward DFT along l, K_l before and conj(A_l)/N_l after the inverse DFT.
+//  - The multipliers of the method are applied per line: A_l (with the 1/N_l
+//    of the transform pair) before the forward DFT along l, K_l before the
+//    inverse DFT.  Between the stages of one launch the state keeps the
+//    demodulation factor of its last kinetic substep, so the next forward
+//    pass multiplies by A(p) conj(A(p_old)) instead, and only the last kinetic
+//    substep of a launch multiplies by conj(A) after its inverse DFTs.
+//  - 12-point lines use the Good-Thomas 4 x 3 factorisation (no twiddles).
+//  - Each pass is a separate (non-inlined) function, so that its register
+//    allocation does not carry the persistent loop's live values.
 //  - The potential phase e^{-i sigma V(x^J)/hbar} (eq:U_V_tensor) is a product
 //    of per-axis factors e^{-i sigma f_a(x_a)/hbar} and nearest-neighbour pair
 //    factors e^{-i sigma h_a(x_a) g_{a+1}(x_{a+1})/hbar}, each tabulated from
@@ -39,9 +46,16 @@
 namespace mgk {
 namespace {
 
-constexpr int short_threads(int n) { return n % 3 == 0 ? 288 : 256; }
+// Threads per CTA (8 or 9 warps, one CTA per SM) and lines per thread (2 for
+// FP32, 1 for FP64); lines per chunk = threads x lines per thread.  Sixteen
+// warps with 128 registers each spill in the fused passes and ran slower.
+constexpr int short_threads(int prec, int n) { return n % 3 == 0 ? 288 : 256; }
+constexpr int short_lpt(int prec, int n) { return prec ? 2 : 1; }
 
 enum { SM_NONE = 0, SM_KIN = 1, SM_V = 2, SM_VONLY = 3 };
+// scalar slots of the short kernel beyond the shared ones: p before the last
+// potential substep
+constexpr int SC_POLD = 48;
 
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies of one element
@@ -102,8 +116,31 @@ template <bool INV, int N, typename V> struct LineDft;
 template <bool INV, typename V> struct LineDft<INV, 8, V> {
   static __device__ __forceinline__ void run(V* x, const V*) { Dft<INV, 8, V>::run(x); }
 };
+// 12 = 4 x 3 with coprime factors (Good-Thomas prime-factor mapping): input
+// index (3 n1 + 4 n2) mod 12, output index k with k mod 4 = k1 and k mod 3 =
+// k2, i.e. (9 k1 + 4 k2) mod 12; no twiddle factors between the stages.
 template <bool INV, typename V> struct LineDft<INV, 12, V> {
-  static __device__ __forceinline__ void run(V* x, const V* tw) { dft2<INV, 4, 3>(x, tw); }
+  static __device__ __forceinline__ void run(V* x, const V*) {
+    V y[12];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+      V t[4];
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) t[n1] = x[(3 * n1 + 4 * n2) % 12];
+      Dft<INV, 4, V>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      V t[3];
+#pragma unroll
+      for (int n2 = 0; n2 < 3; ++n2) t[n2] = y[n2 * 4 + k1];
+      Dft<INV, 3, V>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) x[(9 * k1 + 4 * k2) % 12] = t[k2];
+    }
+  }
 };
 template <bool INV, typename V> struct LineDft<INV, 16, V> {
   static __device__ __forceinline__ void run(V* x, const V* tw) { dft2<INV, 4, 4>(x, tw); }
@@ -175,6 +212,12 @@ template <typename V, typename T> struct SSm {
   T* col;     // [5][D*n] f', g, g', h, h'
   V* reg[3];
 };
+
+// Region k of a chunk ring, chosen with selects (a runtime index into the
+// pointer array would put the array in local memory).
+template <typename V, typename T> __device__ __forceinline__ V* region(const SSm<V, T>& S, int k) {
+  return k == 0 ? S.reg[0] : (k == 1 ? S.reg[1] : S.reg[2]);
+}
 
 template <typename V, typename T>
 __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned char* base) {
@@ -279,6 +322,50 @@ __device__ void build_v_short(const Plan& P, const ShortPlan& SP, const Bufs& B,
   }
 }
 
+// Multipliers of the forward passes and of the final inverse passes.  Between
+// stages of one launch the stored state carries the demodulation factor of
+// the last kinetic substep, w = A(p) u (A as in mg_kernels.cu), which saves
+// the conj(A)/N multiply of every inverse pass but the last:
+//  - pre  (global SP.tabB, shared tA): A(p)/N_l if the state is u (rel = 0),
+//    else A(p) conj(A(p_old))/N_l = e^{-i (p - p_old) c dq/hbar}/N_l (rel = 1),
+//    with p_old the centre before the last potential substep (SC_POLD);
+//  - post (global SP.tabC, shared tAi): conj(A(p)), applied by the inverse
+//    passes of the launch's last kinetic substep only.
+// The 1/N_l of the unitary pair of transforms sits in the forward multiplier.
+template <typename V>
+__device__ void build_demod_short(const Plan& P, const ShortPlan& SP, const Smem<V>& S, int rel) {
+  const int TT = P.tab_total, n = SP.n;
+  const int nch = (TT + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const double* sc = S.sc;
+  for (int t = warp * gridDim.x + blockIdx.x; t < 2 * nch; t += nwarps * gridDim.x) {
+    const int e = (t % nch) * 32 + lane;
+    if (e >= TT) continue;
+    const int a = e / n, j = e - a * n;
+    const double c = (double)(j - n / 2);
+    double sn, cs;
+    if (t < nch) {
+      const double dp = rel ? sc[SC_P + a] - sc[SC_POLD + a] : sc[SC_P + a];
+      expi_prec(P.prec, -dp * c * P.dq[a] / P.hbar, S.sct, sn, cs);
+      const double sg = (!rel && (j & 1)) ? -1.0 : 1.0;
+      const double re = sg * cs / (double)n, im = sg * sn / (double)n;
+      __stcg(SP.tabB + e, P.prec ? round_unit_f32(re, im, 1.0 / ((double)n * (double)n)) : make_double2(re, im));
+    } else {
+      expi_prec(P.prec, -sc[SC_P + a] * c * P.dq[a] / P.hbar, S.sct, sn, cs);
+      const double sg = (j & 1) ? -1.0 : 1.0;
+      __stcg(SP.tabC + e, P.prec ? round_unit_f32(sg * cs, -sg * sn, 1.0) : make_double2(sg * cs, -sg * sn));
+    }
+  }
+}
+
+template <typename V>
+__device__ void load_demod_short(const Plan& P, const ShortPlan& SP, const Smem<V>& S) {
+  for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
+    S.tA[e] = from_d2<V>(__ldcg(SP.tabB + e));
+    S.tAi[e] = from_d2<V>(__ldcg(SP.tabC + e));
+  }
+}
+
 template <typename V, typename T>
 __device__ void load_v_short(const Plan& P, const ShortPlan& SP, const Bufs& B, const SSm<V, T>& S) {
   const int TT = P.tab_total, n = SP.n;
@@ -340,44 +427,52 @@ __device__ __forceinline__ void chunk_geom(const GroupPlan& G, int64_t c, int64_
   }
 }
 
-template <int N, typename V>
-__device__ __forceinline__ void issue_load(const GroupPlan& G, const V* __restrict__ src, int64_t c, V* reg) {
+// Chunk copies, element by element (cp.async in, streaming stores out).  The
+// element index advances by the CTA size each iteration; the chunk
+// coordinates (row of the group block, plane wt) are carried incrementally,
+// without a division per element.  Element (wt, row) sits at shared index
+// wt * PS + row + row / N (rows padded to N + 1 per last-axis line).
+template <int N, bool STORE, typename V>
+__device__ __forceinline__ void chunk_copy(const GroupPlan& G, V* __restrict__ gmem, int64_t c, V* reg) {
   int64_t gb;
   int nwt;
   chunk_geom(G, c, gb, nwt);
-  const int cnt = nwt * G.ng;
+  const int nt = blockDim.x;
   if (G.contig) {
-    const Div16 dng((unsigned)G.ng);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int wt = (int)dng((unsigned)e), row = e - wt * G.ng;
-      cp_async_el(reg + wt * G.PS + (row / N) * (N + 1) + row % N, src + gb + e);
+    // planes are whole blocks, consecutive in memory: element e = wt * ng + row
+    int wt = threadIdx.x / G.ng, row = threadIdx.x - wt * G.ng;
+    const int dr = nt % G.ng, dw = nt / G.ng;
+    V* g = gmem + gb + threadIdx.x;
+    while (wt < nwt) {
+      V* s = reg + wt * G.PS + row + row / N;
+      if (STORE) __stcs(g, *s);
+      else cp_async_el(s, g);
+      g += nt;
+      row += dr;
+      wt += dw;
+      if (row >= G.ng) {
+        row -= G.ng;
+        ++wt;
+      }
     }
   } else {
-    const Div16 dw((unsigned)G.WT);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int row = (int)dw((unsigned)e), wt = e - row * G.WT;
-      cp_async_el(reg + wt * G.PS + (row / N) * (N + 1) + row % N, src + gb + row * G.inner + wt);
-    }
-  }
-}
-
-template <int N, typename V>
-__device__ __forceinline__ void store_chunk(const GroupPlan& G, V* __restrict__ dst, int64_t c, const V* reg) {
-  int64_t gb;
-  int nwt;
-  chunk_geom(G, c, gb, nwt);
-  const int cnt = nwt * G.ng;
-  if (G.contig) {
-    const Div16 dng((unsigned)G.ng);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int wt = (int)dng((unsigned)e), row = e - wt * G.ng;
-      __stcs(dst + gb + e, reg[wt * G.PS + (row / N) * (N + 1) + row % N]);
-    }
-  } else {
-    const Div16 dw((unsigned)G.WT);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int row = (int)dw((unsigned)e), wt = e - row * G.WT;
-      __stcs(dst + gb + row * G.inner + wt, reg[wt * G.PS + (row / N) * (N + 1) + row % N]);
+    // rows of WT adjacent elements, `inner` apart: element e = row * WT + wt
+    int row = threadIdx.x / G.WT, wt = threadIdx.x - row * G.WT;
+    const int dw = nt % G.WT, dr = nt / G.WT;
+    V* g = gmem + gb + (int64_t)row * G.inner + wt;
+    const int64_t gstep = (int64_t)dr * G.inner + dw, gwrap = G.inner - G.WT;
+    while (row < G.ng) {
+      V* s = reg + wt * G.PS + row + row / N;
+      if (STORE) __stcs(g, *s);
+      else cp_async_el(s, g);
+      g += gstep;
+      row += dr;
+      wt += dw;
+      if (wt >= G.WT) {
+        wt -= G.WT;
+        ++row;
+        g += gwrap;
+      }
     }
   }
 }
@@ -386,13 +481,23 @@ __device__ __forceinline__ void store_chunk(const GroupPlan& G, V* __restrict__ 
 // One group pass
 // ---------------------------------------------------------------------------
 
-template <typename T, int N, bool INV>
-__device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, const SSm<typename VT<T>::v, T>& S,
-                           int gi, int mode, int slot) {
+// One pass over the state for group gi.  MODE: SM_NONE (transforms only),
+// SM_KIN (forward; kinetic moments on the lines along axis 0), SM_V (inverse;
+// potential phase and moments on the lines along the last axis), SM_VONLY
+// (potential substep alone).  POST: apply the final conj(A) (inverse passes of
+// a launch's last kinetic substep).
+template <typename T, int N, bool INV, int MODE, bool POST>
+__device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B,
+                                       const SSm<typename VT<T>::v, T>& Sref, int gi, int slot) {
+  constexpr int mode = MODE;
   using V = typename VT<T>::v;
-  const GroupPlan& G = SP.grp[gi];
+  // local copies: read through references, the plan (a kernel parameter) and
+  // the shared-memory pointers would be reloaded from memory in every loop
+  const GroupPlan G = SP.grp[gi];
+  const SSm<V, T> S = Sref;
   const int D = P.D, g = G.g, l0 = G.l0;
   const int TT = P.tab_total;
+  const int pairs = SP.pairs;
   V* psi = (V*)B.psi;
   const V* tw = S.s.tw;  // forward twiddles of axis 0 (all axes have n points)
   const int nreg = SP.nreg;
@@ -401,37 +506,37 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
   acc.zero();
 
   for (int s = 0; s < nreg - 1; ++s) {
-    if (s < mine) issue_load<N>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, S.reg[s]);
+    if (s < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s));
     cp_commit();
   }
   for (int64_t i = 0; i < mine; ++i) {
     const int64_t c = blockIdx.x + i * gridDim.x;
     {
       const int64_t i2 = i + nreg - 1;
-      if (i2 < mine) issue_load<N>(G, psi, blockIdx.x + i2 * gridDim.x, S.reg[i2 % nreg]);
+      if (i2 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + i2 * gridDim.x, region(S, (int)(i2 % nreg)));
       cp_commit();
     }
     if (nreg == 3) cp_wait<2>();
     else cp_wait<1>();
     __syncthreads();
-    V* reg = S.reg[i % nreg];
+    V* reg = region(S, (int)(i % nreg));
     int64_t gb;
     int nwt;
     chunk_geom(G, c, gb, nwt);
     const int nl = nwt * ipow<N>(g - 1);  // lines along any group axis
     // first block (contig) or first trailing index (strided) of the chunk
     const unsigned cbase = G.contig ? (unsigned)(c * G.WT) : (unsigned)((c % G.nb) * G.WT);
-    const int kfirst = mode == SM_VONLY ? g - 1 : 0;
-    for (int kk = kfirst; kk < g; ++kk) {
+    const int kend = mode == SM_VONLY ? 0 : g;
+    for (int kk = 0; kk < kend; ++kk) {
       // forward: last axis of the group first; inverse: first axis first
-      const int k = mode == SM_VONLY ? g - 1 : (INV ? kk : g - 1 - kk);
+      const int k = INV ? kk : g - 1 - kk;
       const int a = l0 + k;
       const bool last = (kk == g - 1);
       const int nlo = ipow<N>(g - 1 - k), nhi = ipow<N>(k);
       const int stride = (k == g - 1) ? 1 : ipow<N>(g - 2 - k) * (N + 1);
       const Div16 dlo((unsigned)nlo), dhi((unsigned)nhi);
-      const V* pre = mode == SM_VONLY ? nullptr : (INV ? S.s.tK : S.s.tA) + a * N;
-      const V* post = (mode != SM_VONLY && INV) ? S.s.tAi + a * N : nullptr;
+      const V* pre = (INV ? S.s.tK : S.s.tA) + a * N;
+      const V* post = (INV && POST) ? S.s.tAi + a * N : nullptr;
       for (int L = threadIdx.x; L < nl; L += blockDim.x) {
         const int t = (int)dlo((unsigned)L), lo = L - t * nlo;
         const int wt = (int)dhi((unsigned)t), hi = t - wt * nhi;
@@ -440,11 +545,9 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
         V x[N];
 #pragma unroll
         for (int r = 0; r < N; ++r) x[r] = reg[base + r * stride];
-        if (pre) {
 #pragma unroll
-          for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
-          LineDft<INV, N, V>::run(x, tw);
-        }
+        for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
+        LineDft<INV, N, V>::run(x, tw);
         if (post) {
 #pragma unroll
           for (int r = 0; r < N; ++r) x[r] = cmul(x[r], post[r]);
@@ -466,7 +569,21 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
 #pragma unroll
           for (int b = 1; b < MAXD; ++b)
             if (b < D) acc.add(1 + b, (T)(j[b] - N / 2) * s0);
-        } else if (last && (mode == SM_V || mode == SM_VONLY)) {
+        }
+#pragma unroll
+        for (int r = 0; r < N; ++r) reg[base + r * stride] = x[r];
+      }
+      __syncthreads();
+    }
+    if (mode == SM_V || mode == SM_VONLY) {
+      // potential substep on the lines along the last axis (k = g-1), in a
+      // sweep of its own: the transform loop above keeps fewer registers live
+      const int nhi = ipow<N>(g - 1);
+      const Div16 dhi((unsigned)nhi);
+      for (int L = threadIdx.x; L < nl; L += blockDim.x) {
+        const int wt = (int)dhi((unsigned)L), hi = L - wt * nhi;
+        const int base = wt * G.PS + hi * (N + 1);
+        {
           // potential phase and gradient moments; the line runs along axis D-1
           int j[MAXD];
           if (g >= 2) digits<N>((unsigned)hi, l0, D - 2, j);
@@ -482,7 +599,7 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
           for (int b = 1; b < MAXD - 1; ++b)
             if (b < D - 1) lf = cmul(lf, S.F[b * N + j[b]]);
           const V* prow = nullptr;
-          if (SP.pairs) {
+          if (pairs) {
 #pragma unroll
             for (int b = 0; b < MAXD - 2; ++b)
               if (b < D - 2) lf = cmul(lf, S.Pt[(b * N + j[b]) * N + j[b + 1]]);
@@ -490,16 +607,22 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
           }
           const V* fl = S.F + (D - 1) * N;
           T s0 = 0, sg = 0, sfp = 0, sgp = 0;
-#pragma unroll
+          // element by element from shared memory: nothing of the line is
+          // held in registers
+          const T* lcg = cg + (D - 1) * N;
+          const T* lcfp = cfp + (D - 1) * N;
+          const T* lcgp = cgp + (D - 1) * N;
+#pragma unroll 4
           for (int r = 0; r < N; ++r) {
-            const T w = x[r].x * x[r].x + x[r].y * x[r].y;
+            V xv = reg[base + r];
+            const T w = xv.x * xv.x + xv.y * xv.y;
             s0 += w;
-            sg += cg[(D - 1) * N + r] * w;
-            sfp += cfp[(D - 1) * N + r] * w;
-            sgp += cgp[(D - 1) * N + r] * w;
+            sg += lcg[r] * w;
+            sfp += lcfp[r] * w;
+            sgp += lcgp[r] * w;
             V f = cmul(lf, fl[r]);
             if (prow) f = cmul(f, prow[r]);
-            x[r] = cmul(x[r], f);
+            reg[base + r] = cmul(xv, f);
           }
           acc.add(0, s0);
           // axes whose derivative does not involve the line's coordinate
@@ -517,16 +640,14 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
             acc.add_rt(D, sfp + ch[b * N + jm] * sgp);
           }
         }
-#pragma unroll
-        for (int r = 0; r < N; ++r) reg[base + r * stride] = x[r];
       }
       __syncthreads();
     }
-    store_chunk<N>(G, psi, c, reg);
+    chunk_copy<N, true>(G, psi, c, reg);
     __syncthreads();
   }
   cp_wait<0>();
-  if (mode != SM_NONE) block_record<T>(B, S.s.red, slot, acc, D + 1);
+  if (MODE != SM_NONE) block_record<T>(B, S.s.red, slot, acc, D + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +655,7 @@ __device__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B, co
 // ---------------------------------------------------------------------------
 
 template <typename T, int N>
-__global__ void __launch_bounds__(short_threads(N), 1)
+__global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     k_propagate_short(const __grid_constant__ Plan P, const __grid_constant__ Bufs B,
                       const __grid_constant__ Run RN, const __grid_constant__ ShortPlan SP) {
   using V = typename VT<T>::v;
@@ -550,7 +671,14 @@ __global__ void __launch_bounds__(short_threads(N), 1)
     sc[SC_Q + threadIdx.x] = __ldcg(B.ctrl + threadIdx.x);
     sc[SC_P + threadIdx.x] = __ldcg(B.ctrl + 8 + threadIdx.x);
   }
-  load_tables(P, B, S.s, LT_TW | LT_A | LT_SCT);
+  load_tables(P, B, S.s, LT_TW | LT_SCT);
+  // the state enters as u: forward multiplier A/N = conj(conj(A)/N), final
+  // post-multiplier conj(A), both exact conversions of the context's tables
+  for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
+    const double2 ai = __ldcg(B.tabAi + e), a = __ldcg(B.tabA + e);
+    S.s.tA[e] = from_d2<V>(make_double2(ai.x, -ai.y));
+    S.s.tAi[e] = from_d2<V>(make_double2(a.x, -a.y));
+  }
   __syncthreads();
   const double* gam = B.gamma;
 
@@ -566,14 +694,14 @@ __global__ void __launch_bounds__(short_threads(N), 1)
     if (!grid_sync(B, &sflag)) return;
     load_v_short(P, SP, B, S);
     __syncthreads();
-    short_pass<T, N, false>(P, SP, B, S, 0, SM_VONLY, 1);
+    short_pass<T, N, false, SM_VONLY, false>(P, SP, B, S, 0, 1);
     if (!grid_sync(B, &sflag)) return;
     finish(B, S.s, 1, D + 1);
     centre_after_potential(P, S.s, RN.motion);
     if (sc[SC_ERR] != 0.0) goto done;
-    build_tables(P, B, S.s, TB_A);
+    build_demod_short(P, SP, S.s, 0);  // the state is still u
     if (!grid_sync(B, &sflag)) return;
-    load_tables(P, B, S.s, LT_A);
+    load_demod_short(P, SP, S.s);
     __syncthreads();
   }
 
@@ -589,10 +717,12 @@ __global__ void __launch_bounds__(short_threads(N), 1)
     }
     __syncthreads();
     const bool hasv = sc[SC_HASV] != 0.0;
+    const bool final_unit = (u == RN.n_units - 1);
     // forward transform, group by group from the last axis; kinetic moments
     // in the pass over the group that holds axis 0
     for (int gi = 0; gi < ng; ++gi) {
-      short_pass<T, N, false>(P, SP, B, S, gi, gi == ng - 1 ? SM_KIN : SM_NONE, 0);
+      if (gi == ng - 1) short_pass<T, N, false, SM_KIN, false>(P, SP, B, S, gi, 0);
+      else short_pass<T, N, false, SM_NONE, false>(P, SP, B, S, gi, 0);
       if (!grid_sync(B, &sflag)) return;
     }
     finish(B, S.s, 0, D + 1);
@@ -608,20 +738,34 @@ __global__ void __launch_bounds__(short_threads(N), 1)
     // inverse transform from the group of axis 0; the potential substep is
     // fused into the pass over the group that holds the last axis
     for (int gi = ng - 1; gi >= 0; --gi) {
-      short_pass<T, N, true>(P, SP, B, S, gi, (gi == 0 && hasv) ? SM_V : SM_NONE, 1);
+      const bool v = (gi == 0 && hasv);
+      if (final_unit) {
+        if (v) short_pass<T, N, true, SM_V, true>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, true>(P, SP, B, S, gi, 1);
+      } else {
+        if (v) short_pass<T, N, true, SM_V, false>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, false>(P, SP, B, S, gi, 1);
+      }
       if (gi > 0 && !grid_sync(B, &sflag)) return;
     }
     if (hasv) {
       if (!grid_sync(B, &sflag)) return;
       finish(B, S.s, 1, D + 1);
+      if (threadIdx.x < D) sc[SC_POLD + threadIdx.x] = sc[SC_P + threadIdx.x];
+      __syncthreads();
       centre_after_potential(P, S.s, RN.motion);
       if (sc[SC_ERR] != 0.0) goto done;
-      build_tables(P, B, S.s, TB_A);
-      if (!grid_sync(B, &sflag)) return;
-      load_tables(P, B, S.s, LT_A);
-      __syncthreads();
+      if (!final_unit) {
+        build_demod_short(P, SP, S.s, 1);  // the state carries A(p_old)
+        if (!grid_sync(B, &sflag)) return;
+        load_demod_short(P, SP, S.s);
+        __syncthreads();
+      }
     }
   }
+  // the context's demodulation tables for the final grid centre (read by the
+  // next launch and the observables); the kernel's end orders these writes
+  build_tables(P, B, S.s, TB_A);
 done:
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int a = 0; a < D; ++a) {
@@ -651,6 +795,7 @@ void* short_kernel(int prec, int n) {
   return nullptr;
 }
 
-int short_threads_for(int n) { return short_threads(n); }
+int short_threads_for(int prec, int n) { return short_threads(prec, n); }
+int short_lpt_for(int prec, int n) { return short_lpt(prec, n); }
 
 }  // namespace mgk

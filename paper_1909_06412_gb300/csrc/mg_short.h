@@ -53,6 +53,8 @@ struct ShortPlan {
   int smem_bytes;    // dynamic shared memory per CTA
   int pairs;         // potential has nearest-neighbour pair terms (Henon-Heiles)
   GroupPlan grp[MAXD];
+  double2* tabB;     // [D*n] forward multiplier (A/N or A conj(A_old)/N)
+  double2* tabC;     // [D*n] post-multiplier conj(A) of a launch's last inverse passes
   double2* tabF;     // [D*n] e^{-i sigma f_a(x)/hbar} per axis entry
   double2* tabP;     // [(D-1)*n*n] e^{-i sigma h_a(x_a) g_{a+1}(x_{a+1})/hbar}
 };
