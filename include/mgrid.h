@@ -148,8 +148,10 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
 /* Which propagation kernel mg_propagate uses for this context with its
  * current potential: 1 = the short-axis kernel (D >= 3 axes, all of one
  * length 8, 12 or 16, and a Henon-Heiles or diagonal harmonic potential:
- * several axes transformed per pass over the state), 0 = the general kernel
- * (one pass per axis), -1 for a NULL context or no potential yet.  The same
+ * several axes transformed per pass over the state), 2 = the same kernel
+ * moving its chunks with TMA tensor copies (FP32 storage, 16-point axes),
+ * 0 = the general kernel (one pass per axis), -1 for a NULL context or no
+ * potential yet.  The same
  * method either way (Sec. II.G); only the memory traffic differs.  Setting
  * the environment variable MG_SHORT_AXES=0 before mg_create turns the
  * short-axis kernel off for that context. */

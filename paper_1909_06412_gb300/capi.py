@@ -224,7 +224,7 @@ class Propagator:
 
     @property
     def path(self):
-        """1: mg_propagate runs the short-axis kernel, 0: the general one."""
+        """Kernel of mg_propagate: 0 general, 1 short-axis, 2 short-axis with TMA copies."""
         return int(lib().mg_propagate_path(self._h))
 
 

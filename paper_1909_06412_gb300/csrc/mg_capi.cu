@@ -1,6 +1,7 @@
 // Host side of the C-ABI declared in include/mgrid.h: validation, planning of
 // the axis passes, workspace layout, host-side state preparation (initial
 // wavepackets, composition coefficients) and kernel launches.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,7 +22,7 @@ void* init_tables_kernel(int prec);
 void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
-void* short_kernel(int prec, int n);
+void* short_kernel(int prec, int n, int tma);
 int short_threads_for(int prec, int n);
 int short_lpt_for(int prec, int n);
 }  // namespace mgk
@@ -206,6 +207,31 @@ void tile_plan(Plan& P) {
   }
 }
 
+// Shared memory of the short-axis kernel for regions of `re` elements: sets
+// region_elems, nreg (3 if it fits, else 2) and smem_bytes.  Must match
+// carve_short() in mg_short.cu.
+bool short_smem(const Plan& P, ShortPlan& SP, int re) {
+  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
+  const size_t TT = (size_t)P.tab_total, n = (size_t)SP.n;
+  const size_t tabs = 5 * r16(vs * TT) + r16(sizeof(double2) * 256) + r16(sizeof(double) * 16 * 32) +
+                      r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) + r16(sizeof(uint64_t) * 3) +
+                      r16(sizeof(unsigned) * 4) + r16(vs * (size_t)(P.D - 1) * n * n) + r16(ts * 5 * TT);
+  const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
+  for (int nreg = 3; nreg >= 2; --nreg) {
+    // + up to 1008 bytes per region to start it on a 1024-byte boundary
+    const size_t total = tabs + (size_t)nreg * (r16(vs * (size_t)re) + 1008);
+    if (total <= cap) {
+      SP.region_elems = re;
+      SP.nreg = nreg;
+      SP.smem_bytes = (int)total;
+      return true;
+    }
+  }
+  return false;
+}
+
 // Groups, chunking and shared memory of the short-axis kernel (mg_short.h).
 // A chunk holds lpc lines along any axis of its group (one line per thread
 // for FP64, two for FP32).  The group that ends at the last axis takes the
@@ -272,23 +298,96 @@ bool short_plan(const Plan& P, ShortPlan& SP) {
   SP.threads = threads;
   int re = 0;
   for (int i = 0; i < ngr; ++i) re = std::max(re, SP.grp[i].WT * SP.grp[i].PS);
-  SP.region_elems = re;
-  // must match carve_short() in mg_short.cu
-  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-  const size_t TT = (size_t)P.tab_total;
-  const size_t tabs = 5 * r16(vs * TT) + r16(sizeof(double2) * 256) + r16(sizeof(double) * 16 * 32) +
-                      r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) +
-                      r16(vs * (size_t)(D - 1) * n * n) + r16(ts * 5 * TT);
-  const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
-  for (int nreg = 3; nreg >= 2; --nreg) {
-    const size_t total = tabs + nreg * r16(vs * (size_t)re);
-    if (total <= cap) {
-      SP.nreg = nreg;
-      SP.smem_bytes = (int)total;
-      return true;
-    }
+  return short_smem(P, SP, re);
+}
+
+// TMA tensor maps of the short-axis kernel's chunks (FP32 storage, 16-point
+// axes, a three-axis group at the end and groups of one or two axes before
+// it).  cuTensorMapEncodeTiled comes from the driver through the runtime's
+// entry-point query, so the library links no driver stub.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
   }
-  return false;
+  return fn;
+}
+
+bool short_tma_maps(const Plan& P, ShortPlan& SP, void* psi) {
+  static_assert(sizeof(TensorMapBytes) == sizeof(CUtensorMap), "tensor map size");
+  if (P.prec != 1 || SP.n != 16) return false;
+  const int D = P.D;
+  const GroupPlan& G0 = SP.grp[0];
+  if (!G0.contig || G0.g != 3 || ((uintptr_t)psi & 15)) return false;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const int n = 16;
+  const size_t es = sizeof(float2);
+  for (int gi = 0; gi < SP.ngroups; ++gi) {
+    const GroupPlan& G = SP.grp[gi];
+    cuuint64_t dim[5], str[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    int rank;
+    CUtensorMapSwizzle sw;
+    if (gi == 0) {
+      rank = 4;
+      dim[0] = dim[1] = dim[2] = n;
+      dim[3] = (cuuint64_t)G.nblk;
+      str[0] = n * es;
+      str[1] = n * n * es;
+      str[2] = (cuuint64_t)n * n * n * es;
+      box[0] = box[1] = box[2] = n;
+      box[3] = (cuuint32_t)G.WT;
+      sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    } else {
+      if (G.contig || G.g > 2) return false;
+      const int64_t WP = std::min<int64_t>(G.WT, 256);
+      if (G.WT % WP || (WP * es) % 16) return false;
+      rank = 0;
+      dim[rank] = (cuuint64_t)G.inner;
+      box[rank++] = (cuuint32_t)WP;
+      int64_t s = G.inner;
+      for (int k = 0; k < G.g; ++k) {  // the group's axes, last first
+        str[rank - 1] = (cuuint64_t)(s * es);
+        dim[rank] = n;
+        box[rank++] = n;
+        s *= n;
+      }
+      if (G.l0 > 0) {
+        str[rank - 1] = (cuuint64_t)(s * es);
+        dim[rank] = (cuuint64_t)(P.npts / s);
+        box[rank++] = 1;
+      }
+      sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    }
+    for (int r = 0; r < rank; ++r)
+      if (dim[r] > (1ull << 32)) return false;
+    CUresult r = enc((CUtensorMap*)&SP.tmap[gi], CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, psi, dim, str, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    SP.trank[gi] = rank;
+  }
+  (void)D;
+  return true;
+}
+
+// Regions of the TMA layouts are unpadded: WT blocks of n^g, or n^g rows of
+// WT elements.  Recomputes region size, depth and shared memory for them.
+bool short_tma_smem(const Plan& P, ShortPlan& SP) {
+  int re = 0;
+  for (int i = 0; i < SP.ngroups; ++i) re = std::max(re, SP.grp[i].WT * SP.grp[i].ng);
+  return short_smem(P, SP, re);
 }
 
 // ---- composition coefficients (eq:comp_TVT; Yoshida 1990 triple jump,
@@ -565,7 +664,9 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
   // short-axis kernel: one CTA per SM, all co-resident
   const char* se = std::getenv("MG_SHORT_AXES");
   if ((!se || std::atoi(se) != 0) && short_plan(P, c->SP)) {
-    void* fn = short_kernel(P.prec, c->SP.n);
+    c->SP.tma = short_tma_maps(P, c->SP, d_psi) ? 1 : 0;
+    if (c->SP.tma && !short_tma_smem(P, c->SP)) c->SP.tma = 0;
+    void* fn = short_kernel(P.prec, c->SP.n, c->SP.tma);
     int occ = 0;
     if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->SP.smem_bytes) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->SP.threads, c->SP.smem_bytes) == cudaSuccess &&
@@ -777,7 +878,7 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
   if (c->SP.on && uses_short_kernel(c->P)) {
     ShortPlan SP = c->SP;
     SP.pairs = c->P.pot_kind == MG_POT_HENON_HEILES;
-    void* sfn = short_kernel(c->P.prec, SP.n);
+    void* sfn = short_kernel(c->P.prec, SP.n, SP.tma);
     void* sargs[] = {&c->P, &c->B, &R, &SP};
     cudaError_t e = cudaLaunchCooperativeKernel(sfn, dim3(SP.nblocks), dim3(SP.threads), sargs, SP.smem_bytes,
                                                 c->stream);
@@ -958,7 +1059,8 @@ int64_t mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : -1; }
 
 int mg_propagate_path(const mg_ctx* c) {
   if (!c || !c->pot_set) return -1;
-  return (c->SP.on && uses_short_kernel(c->P)) ? 1 : 0;
+  if (!c->SP.on || !uses_short_kernel(c->P)) return 0;
+  return c->SP.tma ? 2 : 1;
 }
 
 const char* mg_status_string(int s) {

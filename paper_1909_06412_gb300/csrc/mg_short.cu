@@ -241,14 +241,24 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   s.red = (double*)take(sizeof(double) * 16 * 32);
   s.fin = (double*)take(sizeof(double) * PSTRIDE);
   s.sc = (double*)take(sizeof(double) * SC_N);
-  s.mbar = nullptr;
-  s.mphase = nullptr;
+  s.mbar = (uint64_t*)take(sizeof(uint64_t) * 3);
+  s.mphase = (unsigned*)take(sizeof(unsigned) * 4);
   s.tb = nullptr;
   s.li = nullptr;
   m.F = (V*)take(sizeof(V) * TT);
   m.Pt = (V*)take(sizeof(V) * (P.D - 1) * n * n);
   m.col = (T*)take(sizeof(T) * 5 * TT);
-  for (int r = 0; r < 3; ++r) m.reg[r] = r < SP.nreg ? (V*)take(sizeof(V) * SP.region_elems) : nullptr;
+  // chunk regions start on 1024-byte boundaries (the period of the 128-byte
+  // swizzle of the tensor copies)
+  for (int r = 0; r < 3; ++r) {
+    if (r < SP.nreg) {
+      const uintptr_t a = (uintptr_t)(base + off);
+      off += ((a + 1023) & ~(uintptr_t)1023) - a;
+      m.reg[r] = (V*)take(sizeof(V) * SP.region_elems);
+    } else {
+      m.reg[r] = nullptr;
+    }
+  }
   s.reg[0] = m.reg[0];
   s.reg[1] = m.reg[1];
   s.reg[2] = m.reg[2];
@@ -481,12 +491,108 @@ __device__ __forceinline__ void chunk_copy(const GroupPlan& G, V* __restrict__ g
 // One group pass
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// TMA tensor copies of whole chunks (FP32 storage, 16-point axes)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tma_load(const void* tm, int rank, void* dst, uint64_t* bar, const int* c) {
+  const unsigned d = smem_u32(dst), b = smem_u32(bar);
+  if (rank == 2)
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(d), "l"(tm), "r"(c[0]), "r"(c[1]), "r"(b) : "memory");
+  else if (rank == 3)
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(d), "l"(tm), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(b) : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(d), "l"(tm), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(b) : "memory");
+}
+__device__ __forceinline__ void tma_store(const void* tm, int rank, const void* src, const int* c) {
+  const unsigned s = smem_u32(src);
+  if (rank == 2)
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(tm), "r"(c[0]), "r"(c[1]), "r"(s) : "memory");
+  else if (rank == 3)
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(tm), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(s) : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+                 ::"l"(tm), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(s) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Wait for the tensor copies of a chunk, bounded like every wait here: gives
+// up after the barrier time limit (recording MG_ERR_TIMEOUT), or at once when
+// another wait has already failed, so that a failure costs one time limit and
+// not one per chunk.
+__device__ __forceinline__ void wait_chunk(const Bufs& B, uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return;
+  const uint64_t t0 = global_ns();
+  for (unsigned spins = 1;; ++spins) {
+    if (mbar_try_wait(bar, parity)) return;
+    if ((spins & 255u) == 0) {
+      if (*(volatile int*)B.status != ST_OK) return;
+      if (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS) {
+        atomicExch(B.status, ST_TIMEOUT);
+        return;
+      }
+    }
+  }
+}
+
+// One chunk by tensor copies (issued by one thread).  Group 0: one box of WT
+// whole 16x16x16 blocks.  Strided groups: WT / WP boxes of WP adjacent values of
+// the trailing index, each landing as its own plane [row][w] of ng x WP.
+// `store` = false: load into `reg`, completing on `bar`; true: store `reg`.
+template <typename V>
+__device__ __forceinline__ void tma_chunk(const ShortPlan& SP, const GroupPlan& G, int gi, int64_t c, V* reg,
+                                          uint64_t* bar, bool store) {
+  const void* tm = &SP.tmap[gi];
+  const int rank = SP.trank[gi];
+  int cc[5] = {0, 0, 0, 0, 0};
+  if (gi == 0) {
+    cc[3] = (int)(c * G.WT);
+    if (store) {
+      tma_store(tm, rank, reg, cc);
+    } else {
+      mbar_expect_tx(bar, (unsigned)(G.WT * G.ng * sizeof(V)));
+      tma_load(tm, rank, reg, bar, cc);
+    }
+    return;
+  }
+  const int WP = G.WT < 256 ? G.WT : 256;
+  const int64_t o = c / G.nb, b = c - o * G.nb;
+  if (G.l0 > 0) cc[rank - 1] = (int)o;
+  if (!store) mbar_expect_tx(bar, (unsigned)(G.WT * G.ng * sizeof(V)));
+  for (int p = 0; p * WP < G.WT; ++p) {
+    cc[0] = (int)(b * G.WT + p * WP);
+    V* dst = reg + p * G.ng * WP;
+    if (store) tma_store(tm, rank, dst, cc);
+    else tma_load(tm, rank, dst, bar, cc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One group pass
+// ---------------------------------------------------------------------------
+
+// Shared-memory element of point r of line (wt, hi, lo) along group axis k in
+// the 128-byte-swizzled layout of a 16x16x16 block (TMA copies of group 0):
+// row R (one last-axis line, 128 bytes), word w, 16-byte chunk w/2 stored at
+// chunk (w/2) ^ (R mod 8).
+__device__ __forceinline__ int swz(int R, int w) { return R * 16 + ((((w >> 1) ^ R) & 7) << 1) + (w & 1); }
+
 // One pass over the state for group gi.  MODE: SM_NONE (transforms only),
 // SM_KIN (forward; kinetic moments on the lines along axis 0), SM_V (inverse;
 // potential phase and moments on the lines along the last axis), SM_VONLY
 // (potential substep alone).  POST: apply the final conj(A) (inverse passes of
-// a launch's last kinetic substep).
-template <typename T, int N, bool INV, int MODE, bool POST>
+// a launch's last kinetic substep).  TMA: chunks move by tensor copies (FP32,
+// 16-point axes; group 0 swizzled, other groups [plane][row][w]); else by
+// cp.async into the padded plane layout.
+template <typename T, int N, bool INV, int MODE, bool POST, bool TMA>
 __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B,
                                        const SSm<typename VT<T>::v, T>& Sref, int gi, int slot) {
   constexpr int mode = MODE;
@@ -502,24 +608,48 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   const V* tw = S.s.tw;  // forward twiddles of axis 0 (all axes have n points)
   const int nreg = SP.nreg;
   const int64_t mine = blockIdx.x < G.nchunks ? (G.nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  // layouts: 0 padded planes (cp.async), 1 swizzled blocks, 2 [plane][row][w]
+  const int lay = TMA ? (gi == 0 ? 1 : 2) : 0;
+  const int WP = lay == 2 ? (G.WT < 256 ? G.WT : 256) : 1;
+  unsigned parity = TMA ? *S.s.mphase : 0u;
   LineAcc<T> acc;
   acc.zero();
 
   for (int s = 0; s < nreg - 1; ++s) {
-    if (s < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s));
-    cp_commit();
+    if (TMA) {
+      if (threadIdx.x == 0 && s < mine)
+        tma_chunk(SP, G, gi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s), S.s.mbar + s, false);
+    } else {
+      if (s < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s));
+      cp_commit();
+    }
   }
   for (int64_t i = 0; i < mine; ++i) {
     const int64_t c = blockIdx.x + i * gridDim.x;
+    const int ri = (int)(i % nreg);
     {
       const int64_t i2 = i + nreg - 1;
-      if (i2 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + i2 * gridDim.x, region(S, (int)(i2 % nreg)));
-      cp_commit();
+      const int r2 = (int)(i2 % nreg);
+      if (TMA) {
+        if (threadIdx.x == 0 && i2 < mine) {
+          bulk_wait_read0();  // the store that last read region r2 is done with it
+          fence_proxy_async();
+          tma_chunk(SP, G, gi, blockIdx.x + i2 * gridDim.x, region(S, r2), S.s.mbar + r2, false);
+        }
+      } else {
+        if (i2 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + i2 * gridDim.x, region(S, r2));
+        cp_commit();
+      }
     }
-    if (nreg == 3) cp_wait<2>();
-    else cp_wait<1>();
-    __syncthreads();
-    V* reg = region(S, (int)(i % nreg));
+    if (TMA) {
+      wait_chunk(B, S.s.mbar + ri, (parity >> ri) & 1u);
+      parity ^= 1u << ri;
+    } else {
+      if (nreg == 3) cp_wait<2>();
+      else cp_wait<1>();
+      __syncthreads();
+    }
+    V* reg = region(S, ri);
     int64_t gb;
     int nwt;
     chunk_geom(G, c, gb, nwt);
@@ -533,18 +663,53 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       const int a = l0 + k;
       const bool last = (kk == g - 1);
       const int nlo = ipow<N>(g - 1 - k), nhi = ipow<N>(k);
-      const int stride = (k == g - 1) ? 1 : ipow<N>(g - 2 - k) * (N + 1);
-      const Div16 dlo((unsigned)nlo), dhi((unsigned)nhi);
+      const Div16 dlo((unsigned)nlo), dhi((unsigned)nhi), dwp((unsigned)WP);
       const V* pre = (INV ? S.s.tK : S.s.tA) + a * N;
       const V* post = (INV && POST) ? S.s.tAi + a * N : nullptr;
+      // element addressing: linear (base + r * stride) except for the swizzled
+      // layout along its last two axes
+      const int kind = (lay == 1 && k == g - 1) ? 2 : ((lay == 1 && k == g - 2) ? 1 : 0);
       for (int L = threadIdx.x; L < nl; L += blockDim.x) {
-        const int t = (int)dlo((unsigned)L), lo = L - t * nlo;
-        const int wt = (int)dhi((unsigned)t), hi = t - wt * nhi;
-        const int base = wt * G.PS +
-                         (k == g - 1 ? hi * (N + 1) : (hi * nlo + lo / N) * (N + 1) + lo % N);
+        int wt, hi, lo, base = 0, stride = 0;
+        if (lay == 2) {
+          const int t0 = (int)dwp((unsigned)L), w = L - t0 * WP;
+          const int t = (int)dlo((unsigned)t0);
+          lo = t0 - t * nlo;
+          const int piece = (int)dhi((unsigned)t);
+          hi = t - piece * nhi;
+          wt = piece * WP + w;
+          base = piece * G.ng * WP + (hi * nlo * N + lo) * WP + w;
+          stride = nlo * WP;
+        } else {
+          const int t = (int)dlo((unsigned)L);
+          lo = L - t * nlo;
+          wt = (int)dhi((unsigned)t);
+          hi = t - wt * nhi;
+          if (lay == 0) {
+            base = wt * G.PS + (k == g - 1 ? hi * (N + 1) : (hi * nlo + lo / N) * (N + 1) + lo % N);
+            stride = (k == g - 1) ? 1 : ipow<N>(g - 2 - k) * (N + 1);
+          } else if (kind == 0) {  // swizzled, k = 0 of a 3-axis block: rows R = (wt*16 + r)*16 + lo/16
+            base = swz((wt * N) * N + (lo >> 4), lo & 15);
+            stride = N * N;
+          }
+        }
         V x[N];
+        if (kind == 0) {
 #pragma unroll
-        for (int r = 0; r < N; ++r) x[r] = reg[base + r * stride];
+          for (int r = 0; r < N; ++r) x[r] = reg[base + r * stride];
+        } else if (kind == 1) {  // rows R = (wt*16 + hi)*16 + r, word lo
+          const int rb = (wt * N + hi) * N;
+#pragma unroll
+          for (int r = 0; r < N; ++r) x[r] = reg[swz(rb + r, lo)];
+        } else {  // row R = wt*256 + hi, the whole line: 16-byte pairs
+          const int R = wt * N * N + hi;
+#pragma unroll
+          for (int cp = 0; cp < N / 2; ++cp) {
+            const float4 v2 = *reinterpret_cast<const float4*>(reg + swz(R, 2 * cp));
+            x[2 * cp] = V{(T)v2.x, (T)v2.y};
+            x[2 * cp + 1] = V{(T)v2.z, (T)v2.w};
+          }
+        }
 #pragma unroll
         for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
         LineDft<INV, N, V>::run(x, tw);
@@ -570,19 +735,32 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           for (int b = 1; b < MAXD; ++b)
             if (b < D) acc.add(1 + b, (T)(j[b] - N / 2) * s0);
         }
+        if (kind == 0) {
 #pragma unroll
-        for (int r = 0; r < N; ++r) reg[base + r * stride] = x[r];
+          for (int r = 0; r < N; ++r) reg[base + r * stride] = x[r];
+        } else if (kind == 1) {
+          const int rb = (wt * N + hi) * N;
+#pragma unroll
+          for (int r = 0; r < N; ++r) reg[swz(rb + r, lo)] = x[r];
+        } else {
+          const int R = wt * N * N + hi;
+#pragma unroll
+          for (int cp = 0; cp < N / 2; ++cp)
+            *reinterpret_cast<float4*>(reg + swz(R, 2 * cp)) =
+                make_float4((float)x[2 * cp].x, (float)x[2 * cp].y, (float)x[2 * cp + 1].x, (float)x[2 * cp + 1].y);
+        }
       }
       __syncthreads();
     }
     if (mode == SM_V || mode == SM_VONLY) {
-      // potential substep on the lines along the last axis (k = g-1), in a
-      // sweep of its own: the transform loop above keeps fewer registers live
+      // potential substep on the lines along the last axis (k = g-1, group 0),
+      // in a sweep of its own: the transform loop above keeps fewer registers live
       const int nhi = ipow<N>(g - 1);
       const Div16 dhi((unsigned)nhi);
       for (int L = threadIdx.x; L < nl; L += blockDim.x) {
         const int wt = (int)dhi((unsigned)L), hi = L - wt * nhi;
-        const int base = wt * G.PS + hi * (N + 1);
+        const int base = wt * G.PS + hi * (N + 1);  // padded layout
+        const int R = wt * N * N + hi;              // swizzled layout (3-axis block)
         {
           // potential phase and gradient moments; the line runs along axis D-1
           int j[MAXD];
@@ -614,7 +792,8 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           const T* lcgp = cgp + (D - 1) * N;
 #pragma unroll 4
           for (int r = 0; r < N; ++r) {
-            V xv = reg[base + r];
+            const int e = TMA ? swz(R, r) : base + r;
+            V xv = reg[e];
             const T w = xv.x * xv.x + xv.y * xv.y;
             s0 += w;
             sg += lcg[r] * w;
@@ -622,7 +801,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
             sgp += lcgp[r] * w;
             V f = cmul(lf, fl[r]);
             if (prow) f = cmul(f, prow[r]);
-            reg[base + r] = cmul(xv, f);
+            reg[e] = cmul(xv, f);
           }
           acc.add(0, s0);
           // axes whose derivative does not involve the line's coordinate
@@ -643,10 +822,29 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       }
       __syncthreads();
     }
-    chunk_copy<N, true>(G, psi, c, reg);
-    __syncthreads();
+    if (TMA) {
+      // the threads' shared-memory writes before the tensor store reads them
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tma_chunk(SP, G, gi, c, reg, nullptr, true);
+        bulk_commit();
+      }
+    } else {
+      chunk_copy<N, true>(G, psi, c, reg);
+      __syncthreads();
+    }
   }
-  cp_wait<0>();
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      bulk_wait0();  // every store of the pass has reached global memory
+      fence_proxy_async_all();
+      *S.s.mphase = parity;
+    }
+    __syncthreads();
+  } else {
+    cp_wait<0>();
+  }
   if (MODE != SM_NONE) block_record<T>(B, S.s.red, slot, acc, D + 1);
 }
 
@@ -654,7 +852,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
 // The persistent kernel
 // ---------------------------------------------------------------------------
 
-template <typename T, int N>
+template <typename T, int N, bool TMA>
 __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     k_propagate_short(const __grid_constant__ Plan P, const __grid_constant__ Bufs B,
                       const __grid_constant__ Run RN, const __grid_constant__ ShortPlan SP) {
@@ -672,6 +870,7 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     sc[SC_P + threadIdx.x] = __ldcg(B.ctrl + 8 + threadIdx.x);
   }
   load_tables(P, B, S.s, LT_TW | LT_SCT);
+  if (TMA) init_mbarriers(S.s);
   // the state enters as u: forward multiplier A/N = conj(conj(A)/N), final
   // post-multiplier conj(A), both exact conversions of the context's tables
   for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
@@ -694,7 +893,7 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     if (!grid_sync(B, &sflag)) return;
     load_v_short(P, SP, B, S);
     __syncthreads();
-    short_pass<T, N, false, SM_VONLY, false>(P, SP, B, S, 0, 1);
+    short_pass<T, N, false, SM_VONLY, false, TMA>(P, SP, B, S, 0, 1);
     if (!grid_sync(B, &sflag)) return;
     finish(B, S.s, 1, D + 1);
     centre_after_potential(P, S.s, RN.motion);
@@ -721,8 +920,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     // forward transform, group by group from the last axis; kinetic moments
     // in the pass over the group that holds axis 0
     for (int gi = 0; gi < ng; ++gi) {
-      if (gi == ng - 1) short_pass<T, N, false, SM_KIN, false>(P, SP, B, S, gi, 0);
-      else short_pass<T, N, false, SM_NONE, false>(P, SP, B, S, gi, 0);
+      if (gi == ng - 1) short_pass<T, N, false, SM_KIN, false, TMA>(P, SP, B, S, gi, 0);
+      else short_pass<T, N, false, SM_NONE, false, TMA>(P, SP, B, S, gi, 0);
       if (!grid_sync(B, &sflag)) return;
     }
     finish(B, S.s, 0, D + 1);
@@ -740,11 +939,11 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     for (int gi = ng - 1; gi >= 0; --gi) {
       const bool v = (gi == 0 && hasv);
       if (final_unit) {
-        if (v) short_pass<T, N, true, SM_V, true>(P, SP, B, S, gi, 1);
-        else short_pass<T, N, true, SM_NONE, true>(P, SP, B, S, gi, 1);
+        if (v) short_pass<T, N, true, SM_V, true, TMA>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, true, TMA>(P, SP, B, S, gi, 1);
       } else {
-        if (v) short_pass<T, N, true, SM_V, false>(P, SP, B, S, gi, 1);
-        else short_pass<T, N, true, SM_NONE, false>(P, SP, B, S, gi, 1);
+        if (v) short_pass<T, N, true, SM_V, false, TMA>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, false, TMA>(P, SP, B, S, gi, 1);
       }
       if (gi > 0 && !grid_sync(B, &sflag)) return;
     }
@@ -782,15 +981,17 @@ done:
 // Host-side lookup (C++ linkage, used by mg_capi.cu)
 // ---------------------------------------------------------------------------
 
-// The kernel for FP64 (prec 0) or FP32 (prec 1) storage and axis length n.
-void* short_kernel(int prec, int n) {
+// The kernel for FP64 (prec 0) or FP32 (prec 1) storage and axis length n;
+// tma: the chunk copies use TMA tensor maps (FP32, n = 16 only).
+void* short_kernel(int prec, int n, int tma) {
+  if (tma) return (prec == 1 && n == 16) ? (void*)k_propagate_short<float, 16, true> : nullptr;
   switch (n * 2 + prec) {
-    case 16: return (void*)k_propagate_short<double, 8>;
-    case 17: return (void*)k_propagate_short<float, 8>;
-    case 24: return (void*)k_propagate_short<double, 12>;
-    case 25: return (void*)k_propagate_short<float, 12>;
-    case 32: return (void*)k_propagate_short<double, 16>;
-    case 33: return (void*)k_propagate_short<float, 16>;
+    case 16: return (void*)k_propagate_short<double, 8, false>;
+    case 17: return (void*)k_propagate_short<float, 8, false>;
+    case 24: return (void*)k_propagate_short<double, 12, false>;
+    case 25: return (void*)k_propagate_short<float, 12, false>;
+    case 32: return (void*)k_propagate_short<double, 16, false>;
+    case 33: return (void*)k_propagate_short<float, 16, false>;
   }
   return nullptr;
 }

@@ -42,8 +42,16 @@ struct GroupPlan {
   int64_t nchunks;  // chunks in one pass
 };
 
+// An encoded TMA tensor map (CUtensorMap, 128 bytes, 64-byte aligned): opaque
+// here; the device code only passes its address to cp.async.bulk.tensor.
+struct alignas(64) TensorMapBytes {
+  unsigned char b[128];
+};
+
 struct ShortPlan {
   int on;            // the grid has the short-axis shape and the kernel fits
+  int tma;           // chunks move by TMA tensor copies (FP32, n = 16); else cp.async
+  int trank[MAXD];   // rank of each group's tensor map
   int n;             // axis length
   int ngroups;       // grp[0] ends at the last axis, grp[ngroups-1] starts at axis 0
   int threads;       // threads per CTA
@@ -57,6 +65,12 @@ struct ShortPlan {
   double2* tabC;     // [D*n] post-multiplier conj(A) of a launch's last inverse passes
   double2* tabF;     // [D*n] e^{-i sigma f_a(x)/hbar} per axis entry
   double2* tabP;     // [(D-1)*n*n] e^{-i sigma h_a(x_a) g_{a+1}(x_{a+1})/hbar}
+  // TMA (tma = 1): one tensor map per group over psi.  The group that ends at
+  // the last axis is a rank-4 view {n, n, n, blocks} (innermost first) copied
+  // in boxes of {n, n, n, WT} with the 128-byte swizzle; a strided group is a
+  // view {trailing index, its axes from the last, leading index} copied in
+  // boxes of {WP, n, .., 1}, WP = min(WT, 256), WT / WP boxes per chunk.
+  TensorMapBytes tmap[MAXD];
 };
 
 }  // namespace mgk

@@ -67,12 +67,14 @@ def check(g, o, tol):
 @pytest.mark.parametrize("n,D,prec,steps", [
     (16, 3, 0, 6), (12, 3, 0, 6), (8, 3, 0, 6),      # one group holds every axis
     (16, 3, 1, 6), (12, 3, 1, 6),                    # FP32: chunks only partly filled
+    (16, 5, 1, 1),                                   # TMA copies with a strided group of 2 axes
     (12, 4, 0, 4), (16, 4, 0, 4), (12, 4, 1, 4), (16, 4, 1, 4),
     (12, 5, 0, 1), (8, 5, 1, 4), (8, 6, 0, 2),       # strided groups of 2 and 3 axes
 ])
 def test_short_kernel_henon_heiles_vs_oracle(mg, n, D, prec, steps):
     g, o = hh_pair(mg, n, D, prec)
-    assert g.path == 1
+    # FP32 grids of 16-point axes move their chunks by TMA tensor copies
+    assert g.path == (2 if (prec == 1 and n == 16) else 1)
     g.propagate(steps, 0.02, "suzuki4")
     o.propagate(steps, 0.02, "suzuki4")
     check(g, o, 1e-12 if prec == 0 else 5e-5)
@@ -125,7 +127,7 @@ def test_short_kernel_matches_general_kernel(mg, prec, tol):
         else:
             os.environ["MG_SHORT_AXES"] = old
     gs, _ = hh_pair(mg, 16, 4, prec)
-    assert gg.path == 0 and gs.path == 1
+    assert gg.path == 0 and gs.path == (2 if prec == 1 else 1)
     for g in (gg, gs):
         g.propagate(20, 0.02, "yoshida4")
     a, qa, pa, _ = gs.get_state()
