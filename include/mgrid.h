@@ -57,8 +57,12 @@ enum { MG_FP64 = 0, MG_FP32_MIXED = 1 };
 enum { MG_TVT = 0, MG_VTV = 1, MG_TV = 2 };
 /* ADAPTIVE: q-centre moves with the <p> reduction (eq:eom_qt_case_III_T);
  * ADAPTIVE_CENTRE_P: moves with the p-centre itself (eq:eom_qt_solution_case_III_T);
- * FIXED: centres never move (the conventional split-operator method). */
-enum { MG_GRID_ADAPTIVE = 0, MG_GRID_ADAPTIVE_CENTRE_P = 1, MG_GRID_FIXED = 2 };
+ * FIXED: centres never move (the conventional split-operator method);
+ * NAIVE: the naive adaptive grid of Sec. II.F (eq:naive_wf_solution): every
+ * time step runs on the fixed grid, then the grid moves to the new <q>, <p>
+ * by f~(<q>, <p>) f(q, <p>).  Norm-preserving but not time-reversible
+ * (eq:naive_t_rev_fail); mg_propagate only, one host round trip per step. */
+enum { MG_GRID_ADAPTIVE = 0, MG_GRID_ADAPTIVE_CENTRE_P = 1, MG_GRID_FIXED = 2, MG_GRID_NAIVE = 3 };
 /* Potentials (params layout):
  *  HARMONIC        [K (D*D row-major, symmetric), c (D)]: V = 1/2 (x-c)^T K (x-c)
  *  ATOM_DIATOM     D=2, axes (R, r), [Dm, a, re, A, beta]:
@@ -119,6 +123,15 @@ mg_status mg_get_state(mg_ctx* ctx, double* psi, double* q, double* p, double* t
  * pointer may be NULL. */
 mg_status mg_get_observables(mg_ctx* ctx, double* norm, double* energy, double* mean_q,
                              double* mean_p);
+
+/* Represent the current state on the grid centred at (q, p) instead (host,
+ * D doubles each): u <- f~(q, p) f(q_t, p) u, the exact trigonometric
+ * interpolation of the band-limited state between the two grids
+ * (eq:F_defintion, eq:F_inv_definition; the regridding of Sec. II.F and of
+ * the error norms of Sec. III).  Sets the context's centres to (q, p), leaves
+ * t unchanged, synchronises the stream.  Norm-preserving; a regrid back to
+ * the original centres restores the state to rounding. */
+mg_status mg_regrid(mg_ctx* ctx, const double* q, const double* p);
 
 /* Synchronise the context's stream and report any pending device status. */
 mg_status mg_sync(mg_ctx* ctx);

@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "mgrid_oracle.c")
 
 POT_HARMONIC, POT_ATOM_DIATOM, POT_HENON_HEILES, POT_SECREST_JOHNSON = 0, 1, 2, 3
 SPLIT_TVT, SPLIT_VTV, SPLIT_TV = 0, 1, 2
-GRID_ADAPTIVE, GRID_ADAPTIVE_CENTRE_P, GRID_FIXED = 0, 1, 2
+GRID_ADAPTIVE, GRID_ADAPTIVE_CENTRE_P, GRID_FIXED, GRID_NAIVE = 0, 1, 2, 3
 
 
 def build_command():
@@ -213,8 +213,31 @@ class Grid:
         _check(lib().orc_substep_T(self._h, float(tau), grid_motion), "substep_T")
 
     def propagate(self, n_steps, dt, scheme="strang", split=SPLIT_TVT, grid_motion=GRID_ADAPTIVE):
+        if grid_motion == GRID_NAIVE:
+            for _ in range(int(n_steps)):
+                self.step_naive(dt, scheme, split)
+            return
         rc = lib().orc_propagate(self._h, int(n_steps), float(dt), scheme.encode(), split, grid_motion)
         _check(rc, "propagate")
+
+    def step_naive(self, dt, scheme="strang", split=SPLIT_TVT):
+        """One step of the naive adaptive grid, Sec. II.F, in the paper's
+        order: U(dt; q0, p0) on the fixed grid (eq:naive_wf_solution), then
+        q1 = <q>, p1 = <p> of the propagated state, then the state carried to
+        the new grid by f~(q1, p1) f(q0, p1) (literal eq:F_defintion)."""
+        self.propagate(1, dt, scheme, split, GRID_FIXED)
+        _, _, q1, p1 = self.observables()
+        _, q0, _, t = self.get_state()
+        u1 = self.apply_f(q1, p1, self.apply_f(q0, p1, self.get_u(), -1), +1)
+        self.set_u(u1)
+        self.set_centre(q1, p1, t)
+
+    def set_centre(self, q, p, t):
+        """Move the grid centre without touching the stored samples u."""
+        u = self.get_u()
+        psi = self.get_state()[0]
+        self.set_state(psi, q, p, t)
+        self.set_u(u)
 
     def observables(self):
         n, e = np.zeros(1), np.zeros(1)

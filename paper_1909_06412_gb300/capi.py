@@ -19,7 +19,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_UNSUPPORTED, MG_ERR_CUDA = 0, -1, -2, -3
 MG_ERR_TIMEOUT, MG_ERR_NONFINITE, MG_ERR_UNSTABLE, MG_ERR_STATE = -4, -5, -6, -7
 MG_FP64, MG_FP32_MIXED = 0, 1
 MG_TVT, MG_VTV, MG_TV = 0, 1, 2
-MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED = 0, 1, 2
+MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED, MG_GRID_NAIVE = 0, 1, 2, 3
 MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON = 0, 1, 2, 3
 
 __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "MgError", "lib", "mg_workspace_bytes",
@@ -48,6 +48,7 @@ def lib():
         L.mg_get_state.argtypes = [vp, vp, vp, vp, vp]
         L.mg_get_observables.argtypes = [vp, vp, vp, vp, vp]
         L.mg_sync.argtypes = [vp]
+        L.mg_regrid.argtypes = [vp, vp, vp]
         L.mg_kernel_launches.argtypes = [vp]
         L.mg_kernel_launches.restype = i64
         L.mg_propagate_path.argtypes = [vp]
@@ -65,7 +66,7 @@ def lib():
         L.mg_batch_info.argtypes = [vp, vp, vp, vp, vp]
         L.mg_batch_destroy.argtypes = [vp]
         for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
-                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint",
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint", "mg_regrid",
                      "mg_batch_create", "mg_batch_propagate", "mg_batch_sync", "mg_batch_info",
                      "mg_batch_destroy"):
             getattr(L, name).restype = i32
@@ -183,6 +184,11 @@ class Propagator:
 
     def sync(self):
         _check(lib().mg_sync(self._h), "mg_sync")
+
+    def regrid(self, q, p):
+        """Carry the state onto the grid centred at (q, p) (trigonometric interpolation)."""
+        q, p = _f64(q, self.D), _f64(p, self.D)
+        _check(lib().mg_regrid(self._h, _ptr(q), _ptr(p)), "mg_regrid")
 
     def get_state(self, want_psi=True):
         psi = np.empty(self.N, dtype=np.complex128) if want_psi else None

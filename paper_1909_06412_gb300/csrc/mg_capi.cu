@@ -23,6 +23,7 @@ void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
 void* short_kernel(int prec, int n, int tma);
+void* regrid_kernel(int prec, int kind);
 int short_threads_for(int prec, int n);
 int short_lpt_for(int prec, int n);
 }  // namespace mgk
@@ -857,6 +858,19 @@ mg_status mg_set_separable(mg_ctx* c, const int* kinds, const double* params, co
 mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme, int split, int grid_motion) {
   if (!c || n_steps < 0 || !std::isfinite(dt)) return MG_ERR_ARG;
   if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  if (grid_motion == MG_GRID_NAIVE) {
+    // Sec. II.F: each step on the fixed grid, then the grid moved to the
+    // new <q>, <p> by f~(<q>, <p>) f(q, <p>); host-sequenced, one step at a time
+    if (!scheme_coeffs(scheme, c->gam)) return MG_ERR_ARG;
+    for (int64_t s = 0; s < n_steps; ++s) {
+      mg_status st = mg_propagate(c, 1, dt, scheme, split, MG_GRID_FIXED);
+      double mq[MAXD], mp[MAXD];
+      if (st == MG_OK) st = mg_get_observables(c, nullptr, nullptr, mq, mp);
+      if (st == MG_OK) st = mg_regrid(c, mq, mp);
+      if (st != MG_OK) return st;
+    }
+    return MG_OK;
+  }
   if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
     return MG_ERR_ARG;
   if (!scheme_coeffs(scheme, c->gam)) return MG_ERR_ARG;
@@ -898,6 +912,39 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
   if (e != cudaSuccess) return MG_ERR_CUDA;
   c->t += (double)n_steps * dt;
   return MG_OK;
+}
+
+mg_status mg_regrid(mg_ctx* c, const double* q, const double* p) {
+  if (!c || !q || !p) return MG_ERR_ARG;
+  if (!c->state_set) return MG_ERR_STATE;
+  const int D = c->P.D;
+  for (int a = 0; a < D; ++a)
+    if (!std::isfinite(q[a]) || !std::isfinite(p[a])) return MG_ERR_ARG;
+  mg_status s = refresh_tables(c);
+  if (s != MG_OK) return s;
+  double tgt[16] = {0};
+  for (int a = 0; a < D; ++a) {
+    tgt[a] = q[a];
+    tgt[8 + a] = p[a];
+  }
+  // target centres at ctrl[48..64); the barrier counter starts from zero
+  s = cuda_ok(cudaMemcpyAsync(c->B.ctrl + 48, tgt, sizeof(tgt), cudaMemcpyHostToDevice, c->stream));
+  if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
+  if (s != MG_OK) return s;
+  void* fn = regrid_kernel(c->P.prec, c->pot_set ? c->P.pot_kind : MG_POT_HARMONIC);
+  if (!fn) return MG_ERR_UNSUPPORTED;
+  if (c->P.smem_bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->P.smem_bytes) != cudaSuccess)
+    return MG_ERR_CUDA;
+  void* args[] = {&c->P, &c->B};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, c->P.smem_bytes, c->stream);
+  c->launches++;
+  if (e != cudaSuccess) return MG_ERR_CUDA;
+  for (int a = 0; a < D; ++a) {
+    c->q[a] = q[a];
+    c->p[a] = p[a];
+  }
+  return read_status(c);
 }
 
 mg_status mg_sync(mg_ctx* c) {
