@@ -144,14 +144,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """One process per GPU under torchrun (RANK/WORLD_SIZE/MASTER_* from the
+    environment); (rank, world, local rank, torch.distributed or None)."""
     if n_gpus <= 1 and "RANK" not in os.environ:
         return 0, 1, 0, None
     import torch.distributed as dist
 
-    backend = "nccl"
     dist.init_process_group(backend)
     return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", 0)), dist
+
+
+def job_time_and_units(t_local, units_local, dist, device="cpu"):
+    """Whole-job numbers of independent replicas: the slowest rank's time and
+    the units all ranks processed (no data-path collective: only these two
+    numbers cross ranks)."""
+    if dist is None:
+        return t_local, units_local
+    import torch
+
+    v = torch.tensor([t_local, float(units_local)], dtype=torch.float64, device=device)
+    t = v[:1].clone()
+    u = v[1:].clone()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def run_reference(args):
@@ -549,12 +566,7 @@ def main():
     g.sync()
     launches = g.launches - launches0
     ms = [a.elapsed_time(b) for a, b in times]
-    t_total = sum(ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    units = npts * STEPS_PER_CALL * args.steps * world
+    t_total, units = job_time_and_units(sum(ms) / 1e3, npts * STEPS_PER_CALL * args.steps, dist, device=dev)
     value = units / t_total
 
     # end to end through the C-ABI with host buffers: upload, propagate, read back
