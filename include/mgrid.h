@@ -133,6 +133,17 @@ mg_status mg_get_observables(mg_ctx* ctx, double* norm, double* energy, double* 
  * the original centres restores the state to rounding. */
 mg_status mg_regrid(mg_ctx* ctx, const double* q, const double* p);
 
+/* Inner product <psi_a | psi_b> = prod dq_l sum_J conj(psi_a(x_a^J)) psi_b(x_a^J)
+ * of the states of two contexts with the same axis lengths, spacings,
+ * precision and hbar (eq:scalar_prod), each on its own moving grid: b's
+ * state is carried onto a's grid positions by trigonometric interpolation
+ * with b's own momentum window (eq:F_defintion), in a's workspace.  With a
+ * context holding psi_0 it gives the autocorrelation <psi_0 | psi_t>; for
+ * two propagated states it shows that the moving grid does not conserve
+ * the inner product exactly (Sec. II.E).  Neither state changes; both
+ * streams are synchronised.  MG_ERR_ARG for mismatched grids. */
+mg_status mg_inner_product(mg_ctx* a, const mg_ctx* b, double* re, double* im);
+
 /* Synchronise the context's stream and report any pending device status. */
 mg_status mg_sync(mg_ctx* ctx);
 

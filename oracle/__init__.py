@@ -122,6 +122,18 @@ def scheme(name):
     return buf[:s].copy()
 
 
+def inner_product(ga, gb):
+    """<psi_a | psi_b> of two oracle states on grids of the same shape and
+    spacing but different centres (eq:scalar_prod): b's samples are carried
+    onto a's positions with b's momentum window, f~(q_a, p_b) f(q_b, p_b)
+    (literal eq:F_defintion), then summed against a's."""
+    ua, ub = ga.get_u(), gb.get_u()
+    _, qa, _, _ = ga.get_state()
+    _, qb, pb, _ = gb.get_state()
+    ub_on_a = ga.apply_f(qa, pb, ga.apply_f(qb, pb, ub, -1), +1)
+    return complex(np.vdot(ua, ub_on_a))
+
+
 def morse_mean(Dm, a, re, mass, hbar=1.0):
     return lib().orc_morse_mean(Dm, a, re, mass, hbar)
 

@@ -49,6 +49,7 @@ def lib():
         L.mg_get_observables.argtypes = [vp, vp, vp, vp, vp]
         L.mg_sync.argtypes = [vp]
         L.mg_regrid.argtypes = [vp, vp, vp]
+        L.mg_inner_product.argtypes = [vp, vp, vp, vp]
         L.mg_kernel_launches.argtypes = [vp]
         L.mg_kernel_launches.restype = i64
         L.mg_propagate_path.argtypes = [vp]
@@ -66,7 +67,7 @@ def lib():
         L.mg_batch_info.argtypes = [vp, vp, vp, vp, vp]
         L.mg_batch_destroy.argtypes = [vp]
         for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
-                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint", "mg_regrid",
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint", "mg_regrid", "mg_inner_product",
                      "mg_batch_create", "mg_batch_propagate", "mg_batch_sync", "mg_batch_info",
                      "mg_batch_destroy"):
             getattr(L, name).restype = i32
@@ -184,6 +185,12 @@ class Propagator:
 
     def sync(self):
         _check(lib().mg_sync(self._h), "mg_sync")
+
+    def inner_product(self, other):
+        """<psi_self | psi_other>, other's state interpolated onto this grid."""
+        re, im = np.zeros(1), np.zeros(1)
+        _check(lib().mg_inner_product(self._h, other._h, _ptr(re), _ptr(im)), "mg_inner_product")
+        return complex(re[0], im[0])
 
     def regrid(self, q, p):
         """Carry the state onto the grid centred at (q, p) (trigonometric interpolation)."""

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mg_plan.h"
+#include "mg_regrid.h"
 #include "mg_short.h"
 #include "mgrid.h"
 
@@ -24,6 +25,7 @@ void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
 void* short_kernel(int prec, int n, int tma);
 void* regrid_kernel(int prec, int kind);
+void* inner_kernel(int prec);
 int short_threads_for(int prec, int n);
 int short_lpt_for(int prec, int n);
 }  // namespace mgk
@@ -914,6 +916,26 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
   return MG_OK;
 }
 
+namespace {
+
+// One regrid launch on context c (tables and barrier of c).
+mg_status launch_regrid(mg_ctx* c, const RegridArgs& R) {
+  mg_status s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
+  if (s != MG_OK) return s;
+  void* fn = regrid_kernel(c->P.prec, c->pot_set ? c->P.pot_kind : MG_POT_HARMONIC);
+  if (!fn) return MG_ERR_UNSUPPORTED;
+  if (c->P.smem_bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->P.smem_bytes) != cudaSuccess)
+    return MG_ERR_CUDA;
+  RegridArgs r = R;
+  void* args[] = {&c->P, &c->B, &r};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, c->P.smem_bytes, c->stream);
+  c->launches++;
+  return cuda_ok(e);
+}
+
+}  // namespace
+
 mg_status mg_regrid(mg_ctx* c, const double* q, const double* p) {
   if (!c || !q || !p) return MG_ERR_ARG;
   if (!c->state_set) return MG_ERR_STATE;
@@ -922,29 +944,67 @@ mg_status mg_regrid(mg_ctx* c, const double* q, const double* p) {
     if (!std::isfinite(q[a]) || !std::isfinite(p[a])) return MG_ERR_ARG;
   mg_status s = refresh_tables(c);
   if (s != MG_OK) return s;
-  double tgt[16] = {0};
+  RegridArgs R{};
   for (int a = 0; a < D; ++a) {
-    tgt[a] = q[a];
-    tgt[8 + a] = p[a];
+    R.qt[a] = q[a];
+    R.pt[a] = p[a];
   }
-  // target centres at ctrl[48..64); the barrier counter starts from zero
-  s = cuda_ok(cudaMemcpyAsync(c->B.ctrl + 48, tgt, sizeof(tgt), cudaMemcpyHostToDevice, c->stream));
-  if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
+  R.src_ctrl = c->B.ctrl;
+  R.buf = c->B.psi;
+  R.keep_p = 0;
+  R.commit = 1;
+  s = launch_regrid(c, R);
   if (s != MG_OK) return s;
-  void* fn = regrid_kernel(c->P.prec, c->pot_set ? c->P.pot_kind : MG_POT_HARMONIC);
-  if (!fn) return MG_ERR_UNSUPPORTED;
-  if (c->P.smem_bytes > 48 * 1024 &&
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->P.smem_bytes) != cudaSuccess)
-    return MG_ERR_CUDA;
-  void* args[] = {&c->P, &c->B};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, c->P.smem_bytes, c->stream);
-  c->launches++;
-  if (e != cudaSuccess) return MG_ERR_CUDA;
   for (int a = 0; a < D; ++a) {
     c->q[a] = q[a];
     c->p[a] = p[a];
   }
   return read_status(c);
+}
+
+mg_status mg_inner_product(mg_ctx* a, const mg_ctx* b, double* re, double* im) {
+  if (!a || !b || !re || !im) return MG_ERR_ARG;
+  if (!a->state_set || !b->state_set) return MG_ERR_STATE;
+  const Plan &Pa = a->P, &Pb = b->P;
+  if (Pa.D != Pb.D || Pa.prec != Pb.prec || Pa.hbar != Pb.hbar) return MG_ERR_ARG;
+  for (int l = 0; l < Pa.D; ++l)
+    if (Pa.N[l] != Pb.N[l] || Pa.dq[l] != Pb.dq[l]) return MG_ERR_ARG;
+  // b's state, final on its stream, copied into a's scratch and carried onto
+  // a's positions with b's own momentum window
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MG_ERR_CUDA;
+  mg_status s = read_status(a);
+  if (s != MG_OK) return s;
+  const size_t bytes = (size_t)Pa.npts * (Pa.prec == 0 ? sizeof(double2) : sizeof(float2));
+  s = cuda_ok(cudaMemcpyAsync(a->B.scratch, b->B.psi, bytes, cudaMemcpyDeviceToDevice, a->stream));
+  if (s != MG_OK) return s;
+  double qa[16];
+  if (cudaMemcpy(qa, a->B.ctrl, sizeof(qa), cudaMemcpyDeviceToHost) != cudaSuccess) return MG_ERR_CUDA;
+  RegridArgs R{};
+  for (int l = 0; l < Pa.D; ++l) R.qt[l] = qa[l];
+  R.src_ctrl = b->B.ctrl;
+  R.buf = a->B.scratch;
+  R.keep_p = 1;
+  R.commit = 0;
+  s = launch_regrid(a, R);
+  a->tables_stale = true;  // the launch rebuilt a's tables for b's momentum window
+  if (s != MG_OK) return s;
+  void* args[] = {&a->P, &a->B.psi, &a->B.scratch, &a->B.part};
+  if (cudaLaunchKernel(inner_kernel(Pa.prec), dim3(Pa.nblocks), dim3(THREADS), args, 0, a->stream) != cudaSuccess)
+    return MG_ERR_CUDA;
+  a->launches++;
+  s = read_status(a);
+  if (s != MG_OK) return s;
+  std::vector<double> part((size_t)Pa.nblocks * PSTRIDE);
+  if (cudaMemcpy(part.data(), a->B.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MG_ERR_CUDA;
+  double sr = 0, si = 0;
+  for (int k = 0; k < Pa.nblocks; ++k) {
+    sr += part[(size_t)k * PSTRIDE];
+    si += part[(size_t)k * PSTRIDE + 1];
+  }
+  *re = sr;
+  *im = si;
+  return MG_OK;
 }
 
 mg_status mg_sync(mg_ctx* c) {

@@ -14,17 +14,15 @@
 #include <stdint.h>
 
 #include "mg_device.cuh"
+#include "mg_regrid.h"
 
 namespace mgk {
-namespace {
 
-// Target centres in the workspace's control block: q' at ctrl[48..56), p' at
-// ctrl[56..64).
-constexpr int CTRL_TARGET_Q = 48, CTRL_TARGET_P = 56;
+namespace {
 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_regrid(const __grid_constant__ Plan P, const __grid_constant__ Bufs B) {
+    k_regrid(const __grid_constant__ Plan P, const __grid_constant__ Bufs B, const __grid_constant__ RegridArgs R) {
   using V = typename VT<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sflag;
@@ -36,11 +34,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   if (threadIdx.x < D) {
     const int a = threadIdx.x;
-    const double q0 = __ldcg(B.ctrl + a), q1 = __ldcg(B.ctrl + CTRL_TARGET_Q + a);
+    const double q0 = __ldcg(R.src_ctrl + a);
     sc[SC_Q + a] = q0;
-    sc[SC_QN + a] = q1;
-    sc[SC_P + a] = __ldcg(B.ctrl + CTRL_TARGET_P + a);
-    sc[SC_DELTA + a] = q1 - q0;
+    sc[SC_QN + a] = R.qt[a];
+    sc[SC_P + a] = R.keep_p ? __ldcg(R.src_ctrl + 8 + a) : R.pt[a];
+    sc[SC_DELTA + a] = R.qt[a] - q0;
   }
   if (threadIdx.x == 0) sc[SC_TAU] = 0.0;
   load_tables(P, B, S, LT_TW | LT_SCT);
@@ -54,20 +52,51 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int i = 0; i < D; ++i) {
     PassArgs a{};
     a.l = D - 1 - i; a.fft = 1; a.pre = PRE_A;
-    a.src = B.psi; a.dst = B.psi;
+    a.src = R.buf; a.dst = R.buf;
     axis_pass<T, false, KIND>(P, B, a, S, -1);
     if (!grid_sync(B, &sflag)) return;
   }
   for (int i = 0; i < D; ++i) {
     PassArgs a{};
     a.l = i; a.fft = 1; a.pre = PRE_K; a.post = 1;
-    a.src = B.psi; a.dst = B.psi;
+    a.src = R.buf; a.dst = R.buf;
     axis_pass<T, true, KIND>(P, B, a, S, -1);
     if (i + 1 < D && !grid_sync(B, &sflag)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x < D) {
+  if (R.commit && blockIdx.x == 0 && threadIdx.x < D) {
     B.ctrl[threadIdx.x] = sc[SC_QN + threadIdx.x];
     B.ctrl[8 + threadIdx.x] = sc[SC_P + threadIdx.x];
+  }
+}
+
+// Inner product sum_J conj(a_J) b_J of two states on the same grid: FP64
+// per-thread sums, then per-CTA sums in a fixed order into part[cta][0..1]
+// (real, imaginary); the host adds the CTA records in order.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_inner(const __grid_constant__ Plan P, const void* a_, const void* b_,
+                                                    double* part) {
+  using V = typename VT<T>::v;
+  __shared__ double red[2][THREADS / 32];
+  const V* a = (const V*)a_;
+  const V* b = (const V*)b_;
+  double re = 0, im = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.npts; j += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = to_d2(a[j]), y = to_d2(b[j]);
+    re = fma(x.x, y.x, fma(x.y, y.y, re));
+    im = fma(x.x, y.y, fma(-x.y, y.x, im));
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = re;
+    red[1][warp] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+    part[(size_t)blockIdx.x * PSTRIDE + threadIdx.x] = s;
   }
 }
 
@@ -91,5 +120,7 @@ void* regrid_kernel(int prec, int kind) {
   }
   return nullptr;
 }
+
+void* inner_kernel(int prec) { return prec ? (void*)k_inner<float> : (void*)k_inner<double>; }
 
 }  // namespace mgk

@@ -86,3 +86,48 @@ def test_naive_grid_is_not_reversible_on_the_gpu(mg):
         errs[motion] = rel(g.get_state()[0], u0)
     assert errs[mg.MG_GRID_ADAPTIVE] < 1e-12
     assert errs[mg.MG_GRID_NAIVE] > 1e-6
+
+
+def e1_pair(mg, q0, prec=0):
+    P = inputs.DUSCHINSKY3D
+    om = np.array(P["omega"])
+    pot = list(np.array(P["K"]).ravel()) + [0.0] * 3
+    g = mg.Propagator(P["N"], P["dq"], minv=om, precision=prec)
+    g.set_potential(mg.MG_POT_HARMONIC, pot)
+    o = oracle.Grid(P["N"], P["dq"], minv=om)
+    o.set_potential(oracle.POT_HARMONIC, pot)
+    fac = [("gauss", q0[l], 0.0, 1.0) for l in range(3)]
+    g.set_separable(fac, q0, [0.0] * 3)
+    o.set_separable(fac, q0, [0.0] * 3)
+    return g, o
+
+
+def test_inner_product_matches_oracle_and_leaves_both_states(mg):
+    q0 = np.array(inputs.DUSCHINSKY3D["q0"])
+    ga, oa = e1_pair(mg, q0)
+    gb, ob = e1_pair(mg, q0 + np.array([-1.0, 1.0, 1.0]))
+    v = ga.inner_product(gb)
+    assert abs(v - np.exp(-0.75)) < 1e-9          # the printed 0.472 of Sec. III.A
+    for g, o in ((ga, oa), (gb, ob)):
+        g.propagate(7, 0.1, "yoshida4")
+        o.propagate(7, 0.1, "yoshida4")
+    v = ga.inner_product(gb)
+    vo = oracle.inner_product(oa, ob)
+    assert abs(v - vo) < 1e-12 * abs(vo)
+    # neither context was disturbed: both continue exactly like the oracle
+    for g, o in ((ga, oa), (gb, ob)):
+        g.propagate(3, 0.1, "yoshida4")
+        o.propagate(3, 0.1, "yoshida4")
+        psi, q, p, _ = g.get_state()
+        psi_o, q_o, p_o, _ = o.get_state()
+        assert rel(psi, psi_o) < 1e-12 and np.abs(q - q_o).max() < 1e-11
+
+
+def test_inner_product_rejects_mismatched_grids(mg):
+    a = mg.Propagator((16, 16), (0.5, 0.5))
+    b = mg.Propagator((16, 12), (0.5, 0.5))
+    for g in (a, b):
+        g.set_potential(mg.MG_POT_HARMONIC, [1.0, 0.0, 0.0, 1.0, 0.0, 0.0])
+        g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 2, [0.0, 0.0], [0.0, 0.0])
+    with pytest.raises(mg.MgError):
+        a.inner_product(b)
