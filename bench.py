@@ -306,11 +306,15 @@ def other_workloads(mgmod, torch, dev, flush):
         npts = int(np.prod(N))
         ps = npts * steps * stages / t
         D = len(N)
+        hbm_peak, _ = peaks()
+        gbs = ps * 4 * elem / 1e9
+        tf = ps * algorithmic_flops_per_point_stage(N, D) / 1e12 if prec == 0 else None
         out.append({
             "workload": name, "value": npts * steps / t, "unit": UNIT, "points": npts,
             "stages_per_step": stages, "ms_per_step": 1e3 * t / steps,
-            "hbm_gbs_algorithmic": ps * 4 * elem / 1e9,
-            "fp64_tflops_algorithmic": ps * algorithmic_flops_per_point_stage(N, D) / 1e12 if prec == 0 else None,
+            "kernel_path": {0: "general", 1: "short-axis", 2: "short-axis, TMA copies"}.get(g.path, str(g.path)),
+            "hbm_gbs_algorithmic": gbs, "hbm_frac_algorithmic": gbs / hbm_peak,
+            "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / FP64_PEAK_TFLOPS if tf is not None else None,
             "norm_drift": n1 / n0 - 1,
         })
         g.close()
