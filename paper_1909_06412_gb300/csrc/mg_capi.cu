@@ -27,7 +27,7 @@ void* short_kernel(int prec, int n, int tma);
 void* regrid_kernel(int prec, int kind);
 void* inner_kernel(int prec);
 int short_threads_for(int prec, int n);
-int short_lpt_for(int prec, int n);
+int short_lpc_for(int prec, int n);
 }  // namespace mgk
 
 using namespace mgk;
@@ -249,7 +249,7 @@ bool short_plan(const Plan& P, ShortPlan& SP) {
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
   const int threads = short_threads_for(P.prec, n);
-  const int lpc = threads * short_lpt_for(P.prec, n);
+  const int lpc = short_lpc_for(P.prec, n);
   auto pw = [&](int k) {
     int64_t r = 1;
     for (int i = 0; i < k; ++i) r *= n;
@@ -301,7 +301,9 @@ bool short_plan(const Plan& P, ShortPlan& SP) {
   SP.threads = threads;
   int re = 0;
   for (int i = 0; i < ngr; ++i) re = std::max(re, SP.grp[i].WT * SP.grp[i].PS);
-  return short_smem(P, SP, re);
+  if (!short_smem(P, SP, re)) return false;
+  // FP64 12-point lines run two chunks at a time: three regions needed
+  return !(P.prec == 0 && n == 12 && SP.nreg != 3);
 }
 
 // TMA tensor maps of the short-axis kernel's chunks (FP32 storage, 16-point

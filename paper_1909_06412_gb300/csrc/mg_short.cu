@@ -46,11 +46,16 @@
 namespace mgk {
 namespace {
 
-// Threads per CTA (8 or 9 warps, one CTA per SM) and lines per thread (2 for
-// FP32, 1 for FP64); lines per chunk = threads x lines per thread.  Sixteen
-// warps with 128 registers each spill in the fused passes and ran slower.
-constexpr int short_threads(int prec, int n) { return n % 3 == 0 ? 288 : 256; }
-constexpr int short_lpt(int prec, int n) { return prec ? 2 : 1; }
+// Lines along any group axis per chunk (12-point lines: a multiple of 3) and
+// threads per CTA (one CTA per SM).  FP64 12-point chunks (288 lines = 9
+// warp-sets) go two at a time through 12 warps: the FP64 work spreads over
+// the four SM sub-partitions (5 warp-sets on the busiest against 4.5 on
+// average; one chunk on 9 warps puts 3 on one sub-partition against 2.25),
+// and three warps per sub-partition hide FP64 latency (measured: 12 warps
+// beat 9 by 3.5% and 8 by 7%).  Sixteen warps with 128 registers each spill
+// in the fused passes.
+constexpr int short_lpc(int prec, int n) { return n % 3 == 0 ? (prec ? 576 : 288) : (prec ? 512 : 256); }
+constexpr int short_threads(int prec, int n) { return n % 3 == 0 ? (prec ? 288 : 384) : 256; }
 
 enum { SM_NONE = 0, SM_KIN = 1, SM_V = 2, SM_VONLY = 3 };
 // scalar slots of the short kernel beyond the shared ones: p before the last
@@ -615,19 +620,36 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   LineAcc<T> acc;
   acc.zero();
 
-  for (int s = 0; s < nreg - 1; ++s) {
-    if (TMA) {
-      if (threadIdx.x == 0 && s < mine)
-        tma_chunk(SP, G, gi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s), S.s.mbar + s, false);
-    } else {
+  // A "set" is the chunk(s) transformed together: one chunk, or two for FP64
+  // 12-point lines (see short_lpc), whose regions rotate X, Y (set) and Z
+  // (prefetch of the next set's first chunk; its second chunk is loaded into
+  // X as soon as the set is stored).
+  constexpr bool PAIR = !TMA && sizeof(T) == 8 && N == 12;
+  int rx = 0, ry = 1, rz = 2;
+  if (PAIR) {
+    for (int s = 0; s < 2; ++s) {
       if (s < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s));
       cp_commit();
     }
+  } else {
+    for (int s = 0; s < nreg - 1; ++s) {
+      if (TMA) {
+        if (threadIdx.x == 0 && s < mine)
+          tma_chunk(SP, G, gi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s), S.s.mbar + s, false);
+      } else {
+        if (s < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s));
+        cp_commit();
+      }
+    }
   }
-  for (int64_t i = 0; i < mine; ++i) {
-    const int64_t c = blockIdx.x + i * gridDim.x;
+  for (int64_t i = 0; i < mine; i += PAIR ? 2 : 1) {
     const int ri = (int)(i % nreg);
-    {
+    if (PAIR) {
+      if (i + 2 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (i + 2) * gridDim.x, region(S, rz));
+      cp_commit();
+      cp_wait<1>();
+      __syncthreads();
+    } else {
       const int64_t i2 = i + nreg - 1;
       const int r2 = (int)(i2 % nreg);
       if (TMA) {
@@ -636,26 +658,33 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           fence_proxy_async();
           tma_chunk(SP, G, gi, blockIdx.x + i2 * gridDim.x, region(S, r2), S.s.mbar + r2, false);
         }
+        wait_chunk(B, S.s.mbar + ri, (parity >> ri) & 1u);
+        parity ^= 1u << ri;
       } else {
         if (i2 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + i2 * gridDim.x, region(S, r2));
         cp_commit();
+        if (nreg == 3) cp_wait<2>();
+        else cp_wait<1>();
+        __syncthreads();
       }
     }
-    if (TMA) {
-      wait_chunk(B, S.s.mbar + ri, (parity >> ri) & 1u);
-      parity ^= 1u << ri;
-    } else {
-      if (nreg == 3) cp_wait<2>();
-      else cp_wait<1>();
-      __syncthreads();
+    // the set: chunk i (and i+1), its region, lines and first block / index
+    const int ns = (PAIR && i + 1 < mine) ? 2 : 1;
+    V* regs[2];
+    int64_t cs[2];
+    int nls[2];
+    unsigned cbs[2];
+    for (int h = 0; h < 2; ++h) {
+      cs[h] = blockIdx.x + (i + (h < ns ? h : 0)) * gridDim.x;
+      regs[h] = PAIR ? region(S, h ? ry : rx) : region(S, ri);
+      int64_t gb;
+      int nwt;
+      chunk_geom(G, cs[h], gb, nwt);
+      nls[h] = h < ns ? nwt * ipow<N>(g - 1) : 0;  // lines along any group axis
+      // first block (contig) or first trailing index (strided) of the chunk
+      cbs[h] = G.contig ? (unsigned)(cs[h] * G.WT) : (unsigned)((cs[h] % G.nb) * G.WT);
     }
-    V* reg = region(S, ri);
-    int64_t gb;
-    int nwt;
-    chunk_geom(G, c, gb, nwt);
-    const int nl = nwt * ipow<N>(g - 1);  // lines along any group axis
-    // first block (contig) or first trailing index (strided) of the chunk
-    const unsigned cbase = G.contig ? (unsigned)(c * G.WT) : (unsigned)((c % G.nb) * G.WT);
+    const int nl = nls[0] + nls[1];
     const int kend = mode == SM_VONLY ? 0 : g;
     for (int kk = 0; kk < kend; ++kk) {
       // forward: last axis of the group first; inverse: first axis first
@@ -669,7 +698,11 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       // element addressing: linear (base + r * stride) except for the swizzled
       // layout along its last two axes
       const int kind = (lay == 1 && k == g - 1) ? 2 : ((lay == 1 && k == g - 2) ? 1 : 0);
-      for (int L = threadIdx.x; L < nl; L += blockDim.x) {
+      for (int Lset = threadIdx.x; Lset < nl; Lset += blockDim.x) {
+        const int hs = Lset >= nls[0];
+        const int L = Lset - (hs ? nls[0] : 0);
+        V* reg = regs[hs];
+        const unsigned cbase = cbs[hs];
         int wt, hi, lo, base = 0, stride = 0;
         if (lay == 2) {
           const int t0 = (int)dwp((unsigned)L), w = L - t0 * WP;
@@ -757,7 +790,11 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       // in a sweep of its own: the transform loop above keeps fewer registers live
       const int nhi = ipow<N>(g - 1);
       const Div16 dhi((unsigned)nhi);
-      for (int L = threadIdx.x; L < nl; L += blockDim.x) {
+      for (int Lset = threadIdx.x; Lset < nl; Lset += blockDim.x) {
+        const int hs = Lset >= nls[0];
+        const int L = Lset - (hs ? nls[0] : 0);
+        V* reg = regs[hs];
+        const unsigned cbase = cbs[hs];
         const int wt = (int)dhi((unsigned)L), hi = L - wt * nhi;
         const int base = wt * G.PS + hi * (N + 1);  // padded layout
         const int R = wt * N * N + hi;              // swizzled layout (3-axis block)
@@ -827,12 +864,20 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       fence_proxy_async();
       __syncthreads();
       if (threadIdx.x == 0) {
-        tma_chunk(SP, G, gi, c, reg, nullptr, true);
+        tma_chunk(SP, G, gi, cs[0], regs[0], nullptr, true);
         bulk_commit();
       }
     } else {
-      chunk_copy<N, true>(G, psi, c, reg);
+      for (int h = 0; h < ns; ++h) chunk_copy<N, true>(G, psi, cs[h], regs[h]);
       __syncthreads();
+      if (PAIR) {
+        if (i + 3 < mine) chunk_copy<N, false>(G, psi, blockIdx.x + (i + 3) * gridDim.x, region(S, rx));
+        cp_commit();
+        const int t = rx;
+        rx = rz;
+        rz = ry;
+        ry = t;
+      }
     }
   }
   if (TMA) {
@@ -997,6 +1042,6 @@ void* short_kernel(int prec, int n, int tma) {
 }
 
 int short_threads_for(int prec, int n) { return short_threads(prec, n); }
-int short_lpt_for(int prec, int n) { return short_lpt(prec, n); }
+int short_lpc_for(int prec, int n) { return short_lpc(prec, n); }
 
 }  // namespace mgk
