@@ -3,7 +3,7 @@
 import numpy as np
 
 import oracle
-from tests import inputs
+from tests import golden, inputs
 
 P = inputs.DUSCHINSKY3D
 
@@ -25,7 +25,7 @@ def test_initial_overlap_of_the_two_states_on_their_own_grids():
     a, b = e1_state(q0), e1_state(q0 + np.array([-1.0, 1.0, 1.0]))
     v = oracle.inner_product(a, b)
     assert abs(v - np.exp(-0.75)) < 1e-9
-    assert round(abs(v), 3) == 0.472
+    assert round(abs(v), 3) == golden.PAPER["harmonic_overlap"]
     assert abs(oracle.inner_product(b, a) - np.conj(v)) < 1e-13
 
 

@@ -10,7 +10,7 @@ from scipy.linalg import expm
 from scipy.special import digamma
 
 import oracle
-from tests import inputs
+from tests import golden, inputs
 from tests.gaussians import Gauss1D, coherent_state, product_on_grid
 
 
@@ -283,11 +283,12 @@ def duschinsky(K13):
 
 def test_initial_energy_of_the_harmonic_model():
     # Sec. III.A, Fig. 4 caption: E0 = 140.389 n.u.; holds with K13 = +0.017.
+    E0 = golden.PAPER["harmonic_E0"]
     n, E, mq, mp = duschinsky(+0.017).observables()
     assert abs(n - 1) < 1e-9
-    assert abs(E - 140.389) < 6e-4
-    # Table I as printed (K13 = -0.017) gives 142.055 instead.
-    assert abs(duschinsky(-0.017).observables()[1] - 142.055) < 6e-4
+    assert abs(E - E0) < 6e-4
+    # Table I as printed (K13 = -0.017) misses the printed E0 by more than 1.
+    assert abs(duschinsky(-0.017).observables()[1] - E0) > 1.0
 
 
 def test_overlap_harmonic_displaced_ground_state():
@@ -299,7 +300,7 @@ def test_overlap_harmonic_displaced_ground_state():
     g.set_separable([("gauss", d, 0.0, 1.0) for d in (-1, 1, 1)], [0, 0, 0], [0, 0, 0])
     b = g.get_u()
     ov = np.vdot(a, b)
-    assert abs(ov.real - 0.472) < 5e-4 and abs(ov.imag) < 1e-14
+    assert abs(ov.real - golden.PAPER["harmonic_overlap"]) < 5e-4 and abs(ov.imag) < 1e-14
 
 
 def test_overlap_scattering_packets():
@@ -313,7 +314,7 @@ def test_overlap_scattering_packets():
     a = g.get_u()
     g.set_separable([("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.0, s0)], [0, 24], [0, -3.56])
     b = g.get_u()
-    assert abs(abs(np.vdot(a, b)) - 0.534) < 5e-4
+    assert abs(abs(np.vdot(a, b)) - golden.PAPER["scattering_overlap"]) < 5e-4
 
 
 # --------------------------------------------------------------------------
