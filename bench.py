@@ -413,6 +413,110 @@ def adjoint_leg(mgmod, torch, dev):
     return out
 
 
+ORDER_T = 32.0
+ORDER_DTS = (2.0, 1.0, 0.5, 0.25)
+ORDER_SCHEMES = (("strang", 1), ("yoshida4", 3), ("yoshida6", 9), ("yoshida8", 27), ("yoshida10", 81),
+                 ("suzuki4", 5), ("suzuki6", 25))
+ENSEMBLE_MEMBERS = 152
+ENSEMBLE_STEPS = 20
+
+
+def headline_propagator(mgmod, dev, precision=None):
+    fac, qc, pc = initial(mgmod)
+    g = mgmod.Propagator(N_GRID, DQ, minv=MINV, device=dev,
+                         precision=mgmod.MG_FP64 if precision is None else precision)
+    g.set_potential(mgmod.MG_POT_ATOM_DIATOM, POT)
+    g.set_separable(fac, qc, pc)
+    return g
+
+
+def order_leg(mgmod, torch, dev):
+    """Error against composition order and time step on the atom-diatom
+    256 x 256 FP64 workload: every scheme runs to t = ORDER_T a.u. at each
+    time step of ORDER_DTS.  As in the paper's convergence figures (Sec. III),
+    the error of a run is its L2 distance to the run with half the time step,
+    carried onto that run's grid by trigonometric interpolation (mg_regrid);
+    the observed order is log2 of the ratio of successive errors."""
+    out = []
+    npts = int(np.prod(N_GRID))
+    for scheme, stages in ORDER_SCHEMES:
+        runs = []
+        for dt in ORDER_DTS:
+            g = headline_propagator(mgmod, dev)
+            n = int(round(ORDER_T / dt))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(g.stream)
+            g.propagate(n, dt, scheme)
+            e1.record(g.stream)
+            g.sync()
+            runs.append((g, n, e0.elapsed_time(e1)))
+        errs = []
+        for k in range(len(runs) - 1):
+            a, b = runs[k][0], runs[k + 1][0]
+            _, qb, pb, _ = b.get_state(want_psi=False)
+            a.regrid(qb, pb)
+            ua, ub = a.get_state()[0], b.get_state()[0]
+            errs.append(float(np.linalg.norm(ua - ub) / np.linalg.norm(ub)))
+        orders = [math.log2(errs[k] / errs[k + 1]) if min(errs[k], errs[k + 1]) > 1e-11 else None
+                  for k in range(len(errs) - 1)]
+        out.append({"scheme": scheme, "stages_per_step": stages, "dt": list(ORDER_DTS[:-1]), "error": errs,
+                    "observed_order": orders, "ms": [r[2] for r in runs[:-1]],
+                    "gp_stages_per_s": [npts * r[1] * stages / (r[2] / 1e3) for r in runs[:-1]]})
+        for g, _, _ in runs:
+            g.close()
+        del runs
+        torch.cuda.empty_cache()
+    return {"workload": f"collinear atom-diatom 256x256 FP64, t = {ORDER_T} a.u.", "results": out,
+            "error_definition": "||psi(dt) - psi(dt/2)|| / ||psi(dt/2)||, psi(dt) interpolated onto the "
+                                "grid of the dt/2 run"}
+
+
+def ensemble_leg(mgmod, torch, dev):
+    """The headline problem as an ensemble: ENSEMBLE_MEMBERS independent copies
+    in one batched launch (mg_batch_*, FP64), one or two CTAs per member
+    (thread-block clusters of 1 or 2) instead of the whole GPU per member.
+    Reports whole-ensemble throughput, its FP64 roofline fraction and the
+    distance of a member to the single-grid result."""
+    npts = int(np.prod(N_GRID))
+    ref = headline_propagator(mgmod, dev)
+    ref.propagate(2 + ENSEMBLE_STEPS, DT, SCHEME)
+    ref_psi = ref.get_state()[0]
+    ref.close()
+    out = {"workload": f"{ENSEMBLE_MEMBERS} independent members of the headline atom-diatom 256x256 FP64 run, "
+                       f"{SCHEME}, dt = {DT} a.u.", "members": ENSEMBLE_MEMBERS, "steps": ENSEMBLE_STEPS}
+    for cluster in (1, 2):
+        gs = [headline_propagator(mgmod, dev) for _ in range(ENSEMBLE_MEMBERS)]
+        try:
+            b = mgmod.Batch(gs, cluster=cluster)
+        except mgmod.MgError as e:  # a launch shape this GPU cannot place
+            out[f"cluster_{cluster}"] = {"unavailable": str(e)}
+            for g in gs:
+                g.close()
+            continue
+        dts = np.full(ENSEMBLE_MEMBERS, DT)
+        b.propagate(2, dts, SCHEME)
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gs[0].stream)
+        b.propagate(ENSEMBLE_STEPS, dts, SCHEME)
+        e1.record(gs[0].stream)
+        b.sync()
+        t = e0.elapsed_time(e1) / 1e3
+        err = max(float(np.linalg.norm(gs[i].get_state()[0] - ref_psi) / np.linalg.norm(ref_psi))
+                  for i in (0, ENSEMBLE_MEMBERS - 1))
+        v = npts * ENSEMBLE_STEPS * ENSEMBLE_MEMBERS / t
+        tf = v * STAGES * algorithmic_flops_per_point_stage(N_GRID, 2) / 1e12
+        out[f"cluster_{cluster}"] = {"value": v, "unit": UNIT, "s": t, "teams": b.info()["teams"],
+                                     "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / FP64_PEAK_TFLOPS,
+                                     "psi_rel_l2_vs_single_grid": err}
+        b.close()
+        for g in gs:
+            g.close()
+        del gs
+        torch.cuda.empty_cache()
+    return out
+
+
 BATCH_STEPS = 200
 BATCH_SEPARATE_STEPS = 20
 
@@ -603,6 +707,8 @@ def main():
     others = other_workloads(mg, torch, dev, flush)
     adj = adjoint_leg(mg, torch, dev)
     batch = batch_leg(mg, torch, dev)
+    orders = order_leg(mg, torch, dev)
+    ensemble = ensemble_leg(mg, torch, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -631,6 +737,8 @@ def main():
         "other_workloads": others,
         "adjoint": adj,
         "batch": batch,
+        "error_vs_order": orders,
+        "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,

@@ -157,6 +157,39 @@ def test_batch_matches_single_grid_path_on_the_seeded_workload(mg):
         s.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_ensemble_of_the_256x256_atom_diatom_run(mg, cluster):
+    # copies of the 256 x 256 FP64 atom-diatom run (Sec. III.B model, yoshida4,
+    # dt = 1 a.u.) on one or two CTAs each: every member equals the
+    # single-grid result up to the order of the reduction sums
+    N, dq = (256, 256), (0.08, 0.04)
+    amu = 1822.888486
+    pot = [0.17, 1.0, 1.4, 5.0, 1.8]
+
+    def member():
+        g = mg.Propagator(N, dq, minv=(1 / (2.67 * amu), 1 / (0.5 * amu)))
+        g.set_potential(mg.MG_POT_ATOM_DIATOM, pot)
+        rbar = mg.mg_morse_mean(pot[0], pot[1], pot[2], 0.5 * amu)
+        g.set_separable([("gauss", 8.0, -10.0, 0.5), ("morse", pot[0], pot[1], pot[2], 0.5 * amu)],
+                        [8.0, rbar], [-10.0, 0.0])
+        return g
+
+    gs = [member() for _ in range(6)]
+    b = mg.Batch(gs, cluster=cluster)
+    b.propagate(3, 1.0, "yoshida4")
+    b.sync()
+    s = member()
+    s.propagate(3, 1.0, "yoshida4")
+    psi_s, q_s, p_s, _ = state(s)
+    for g in gs:
+        psi, q, p, _ = state(g)
+        assert rel(psi, psi_s) < 1e-13
+        assert np.allclose(q, q_s, rtol=0, atol=1e-13) and np.allclose(p, p_s, rtol=0, atol=1e-12)
+    b.close()
+    for g in gs + [s]:
+        g.close()
+
+
 def test_batch_then_single_grid_continues(mg):
     # after a batched launch the contexts carry on with mg_propagate (their
     # demodulation tables are rebuilt for the moved grid centre)
