@@ -625,9 +625,7 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
     delete c;
     return MG_ERR_CUDA;
   }
-  int per_sm = 1;
-  if (const char* e = std::getenv("MG_BLOCKS_PER_SM")) per_sm = std::max(1, std::atoi(e));
-  P.nblocks = std::min(MAXBLOCKS, sms * per_sm);
+  P.nblocks = std::min(MAXBLOCKS, sms);
   tile_plan(P);
   for (int kind = 0; kind < 4; ++kind) {
     void* fn = propagate_kernel(P.prec, kind);
