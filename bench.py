@@ -274,7 +274,10 @@ def other_workloads(mgmod, torch, dev, flush):
     """The paper's other workload shapes, each timed over one propagate call
     after one warm-up call (state resident in HBM, L2 flushed before the call):
     3D harmonic 32^3 FP64 Strang; 8D Henon-Heiles 12^8 FP64 and 16^8 FP32,
-    fourth-order Suzuki, dt = 0.01."""
+    fourth-order Suzuki, dt = 0.01.  After the timed call: the drifts of the
+    norm and the energy over it, and its reversibility error (the same number
+    of steps back with -dt, then the distance to the state before the timed
+    call, measured on the device)."""
     out = []
     cases = [
         ("3D harmonic 32^3 FP64, strang, dt=0.01", (32, 32, 32), (0.3,) * 3, mgmod.MG_FP64,
@@ -292,9 +295,11 @@ def other_workloads(mgmod, torch, dev, flush):
         g = mgmod.Propagator(N, dq, precision=prec, device=dev)
         g.set_potential(kind, pot)
         g.set_separable(fac, q0, p0)
-        n0 = g.observables()[0]
         g.propagate(1, dt, scheme)
         g.sync()
+        n0, E0 = g.observables()[:2]
+        psi0 = g.psi.clone()
+        _, qs0, ps0, _ = g.get_state(want_psi=False)
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(g.stream)
@@ -302,7 +307,14 @@ def other_workloads(mgmod, torch, dev, flush):
         e1.record(g.stream)
         g.sync()
         t = e0.elapsed_time(e1) / 1e3
-        n1 = g.observables()[0]
+        n1, E1 = g.observables()[:2]
+        g.propagate(steps, -dt, scheme)
+        g.sync()
+        _, qs1, ps1, _ = g.get_state(want_psi=False)
+        ref_norm = float(torch.linalg.vector_norm(psi0))
+        psi0.sub_(g.psi)
+        rev = float(torch.linalg.vector_norm(psi0)) / ref_norm
+        del psi0
         npts = int(np.prod(N))
         ps = npts * steps * stages / t
         D = len(N)
@@ -315,7 +327,9 @@ def other_workloads(mgmod, torch, dev, flush):
             "kernel_path": {0: "general", 1: "short-axis", 2: "short-axis, TMA copies"}.get(g.path, str(g.path)),
             "hbm_gbs_algorithmic": gbs, "hbm_frac_algorithmic": gbs / hbm_peak,
             "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / FP64_PEAK_TFLOPS if tf is not None else None,
-            "norm_drift": n1 / n0 - 1,
+            "norm_drift": n1 / n0 - 1, "energy_drift": E1 / E0 - 1,
+            "reversibility": {"psi_rel_l2": rev, "q_abs": float(np.abs(qs1 - qs0).max()),
+                              "p_abs": float(np.abs(ps1 - ps0).max()), "steps": steps},
         })
         g.close()
         del g
