@@ -263,9 +263,9 @@ __device__ __forceinline__ void expi_tab(double th, const double2* __restrict__ 
 // Grid barrier with a time limit
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint64_t global_ns() {
@@ -279,23 +279,28 @@ constexpr unsigned BARRIER_MAX_SPINS = 400000000u;
 
 // All CTAs of the (cooperative) grid must call this.  Returns false after a
 // timeout; the status word then holds ST_TIMEOUT.
+//
+// One 64-bit word holds the generation (high half) and the arrivals of the
+// current generation (low half).  An arriving CTA adds 1 and learns the
+// generation it arrived in from the returned value; the last arrival adds
+// 2^32 - gridDim.x, which starts the next generation and zeroes the count in
+// one atomic, and the others wait for the generation to change.  The count
+// is back at zero after every completed barrier, so the word needs no reset
+// between launches of any grid size.
 __device__ bool grid_sync(const Bufs& B, int* sflag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned* cnt = B.bar;
-    unsigned* gen = B.bar + 32;
-    const unsigned g0 = ld_acquire_u32(gen);
+    unsigned long long* word = reinterpret_cast<unsigned long long*>(B.bar);
     __threadfence();
-    const unsigned prev = atomicAdd(cnt, 1u);
+    const unsigned long long old = atomicAdd(word, 1ull);
+    const unsigned g0 = (unsigned)(old >> 32);
     int ok = 1;
-    if (prev == gridDim.x - 1) {
-      atomicExch(cnt, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
+    if ((unsigned)old == gridDim.x - 1) {
+      atomicAdd(word, (1ull << 32) - gridDim.x);
     } else {
       const uint64_t t0 = global_ns();
       unsigned spins = 0;
-      while (ld_acquire_u32(gen) == g0) {
+      while ((unsigned)(ld_acquire_u64(word) >> 32) == g0) {
         if (spins > 64) __nanosleep(20);
         ++spins;
         if ((spins & 127u) == 0 && (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS)) {
@@ -377,17 +382,35 @@ enum { LT_TW = 1, LT_A = 2, LT_K = 4, LT_V = 8, LT_C = 16, LT_E = 32, LT_SCT = 6
 // Copy tables from global memory (written by other CTAs) into shared memory.
 template <typename V> __device__ void load_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
   const int TT = P.tab_total;
+  // every load of an entry is issued before its shared-memory stores, so that
+  // the L2 round trips of an entry overlap instead of following one another
   for (int e = threadIdx.x; e < TT; e += blockDim.x) {
-    if (what & LT_TW) S.tw[e] = from_d2<V>(__ldcg(B.tw + e));
+    double2 tw, a, ai, k;
+    double v[NVCOL], cc, ee;
+    if (what & LT_TW) tw = __ldcg(B.tw + e);
     if (what & LT_A) {
-      S.tA[e] = from_d2<V>(__ldcg(B.tabA + e));
-      S.tAi[e] = from_d2<V>(__ldcg(B.tabAi + e));
+      a = __ldcg(B.tabA + e);
+      ai = __ldcg(B.tabAi + e);
     }
-    if (what & LT_K) S.tK[e] = from_d2<V>(__ldcg(B.tabK + e));
-    if (what & LT_V)
-      for (int c = 0; c < NVCOL; ++c) S.tv[c * TT + e] = __ldcg(B.tabV + c * TT + e);
-    if (what & LT_C) S.tc[e] = __ldcg(B.tabC + e);
-    if (what & LT_E) S.te[e] = __ldcg(B.tabE + e);
+    if (what & LT_K) k = __ldcg(B.tabK + e);
+    if (what & LT_V) {
+#pragma unroll
+      for (int c = 0; c < NVCOL; ++c) v[c] = __ldcg(B.tabV + c * TT + e);
+    }
+    if (what & LT_C) cc = __ldcg(B.tabC + e);
+    if (what & LT_E) ee = __ldcg(B.tabE + e);
+    if (what & LT_TW) S.tw[e] = from_d2<V>(tw);
+    if (what & LT_A) {
+      S.tA[e] = from_d2<V>(a);
+      S.tAi[e] = from_d2<V>(ai);
+    }
+    if (what & LT_K) S.tK[e] = from_d2<V>(k);
+    if (what & LT_V) {
+#pragma unroll
+      for (int c = 0; c < NVCOL; ++c) S.tv[c * TT + e] = v[c];
+    }
+    if (what & LT_C) S.tc[e] = cc;
+    if (what & LT_E) S.te[e] = ee;
   }
   if (what & LT_SCT)
     for (int e = threadIdx.x; e < 256; e += blockDim.x) S.sct[e] = __ldcg(B.sct + e);
@@ -711,10 +734,21 @@ __device__ void block_partials(const Bufs& B, const Smem<V>& S, int slot, const 
 // Sum the per-CTA partials of `slot` in a fixed order; result in S.fin.
 template <typename V> __device__ void finish(const Bufs& B, const Smem<V>& S, int slot, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = (int)gridDim.x;
   for (int v = warp; v < nv; v += blockDim.x >> 5) {
+    const double* pv = B.part + (size_t)slot * G * PSTRIDE + v;
     double s = 0;
-    for (int b = lane; b < (int)gridDim.x; b += 32)
-      s += __ldcg(B.part + ((size_t)slot * gridDim.x + b) * PSTRIDE + v);
+    int b = lane;
+    // four loads in flight, added in the same (increasing b) order
+    for (; b + 96 < G; b += 128) {
+      const double x0 = __ldcg(pv + (size_t)b * PSTRIDE), x1 = __ldcg(pv + (size_t)(b + 32) * PSTRIDE);
+      const double x2 = __ldcg(pv + (size_t)(b + 64) * PSTRIDE), x3 = __ldcg(pv + (size_t)(b + 96) * PSTRIDE);
+      s += x0;
+      s += x1;
+      s += x2;
+      s += x3;
+    }
+    for (; b < G; b += 32) s += __ldcg(pv + (size_t)b * PSTRIDE);
     s = warp_sum(s);
     if (lane == 0) S.fin[v] = s;
   }

@@ -58,7 +58,7 @@ struct Plan {
 struct Bufs {
   void* psi;             // scaled state u (complex128 or complex64)
   double* ctrl;          // [0,8) q, [8,16) p, [16] t
-  unsigned* bar;         // [0] arrival count, [32] generation
+  unsigned* bar;         // grid barrier: one 64-bit word (generation, arrivals)
   int* status;
   double* part;          // [2][nblocks][PSTRIDE] per-CTA partial sums
   double2* tw;           // forward twiddles e^{-2 pi i m / N_l}, per axis
