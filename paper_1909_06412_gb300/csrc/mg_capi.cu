@@ -247,7 +247,6 @@ bool short_plan(const Plan& P, ShortPlan& SP) {
   const int n = short_shape(D, P.N);
   if (!n) return false;
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
-  const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
   const int threads = short_threads_for(P.prec, n);
   const int lpc = short_lpc_for(P.prec, n);
   auto pw = [&](int k) {
