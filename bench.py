@@ -43,8 +43,8 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) of one propagate launch, from an ncu capture of
 # `python bench.py --profile`; valid only for the kernel sources it was taken on
 # (sha256 of mg_kernels.cu + mg_device.cuh + mg_plan.h, concatenated).
-TRAFFIC_RECORD = {"kernel_sha256": "d0c871441b7577529f6278a89c7e3fca2d99153c44cfaec6ec11c3e48e5ab968",
-                  "bytes_per_launch": 1.334016e6 + 0.278528e6}
+TRAFFIC_RECORD = {"kernel_sha256": "126437d6a91ba5da12bff0c9b6f24d6b44b5f4622bd81971f34555977fddbee3",
+                  "bytes_per_launch": 1.612544e6 + 0.294400e6}
 KERNEL_SOURCES = ("mg_kernels.cu", "mg_device.cuh", "mg_plan.h")
 
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz

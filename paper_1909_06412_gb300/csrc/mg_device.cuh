@@ -492,10 +492,17 @@ __device__ __forceinline__ void vpoint(const Plan& P, const double* tv, const in
 }
 
 // Potential columns of one table entry (axis a, coordinate x).
-__device__ void vcolumns_eval(const Plan& P, int a, double x, double sgh, double* c) {
-#pragma unroll
-  for (int k = 0; k < NVCOL; ++k) c[k] = 0.0;
+// Part 0 of the columns (0, 1 and 4) or part 1 (2 and 3): the two halves
+// of the evaluation, each with at most half of the exponentials, so that the
+// distributed table build can give them to different warps.
+__device__ void vcolumns_part(const Plan& P, int a, double x, double sgh, int part, double* c) {
+  if (part == 0) {
+    c[0] = c[1] = c[4] = 0.0;
+  } else {
+    c[2] = c[3] = 0.0;
+  }
   if (P.pot_kind == POT_HARMONIC) {
+    if (part) return;
     const double d = x - P.pot[P.D * P.D + a];
     if (!P.pot_general) {
       const double k = P.pot[a * P.D + a];
@@ -508,45 +515,66 @@ __device__ void vcolumns_eval(const Plan& P, int a, double x, double sgh, double
     const double Dm = P.pot[0], aa = P.pot[1], re = P.pot[2], A = P.pot[3], be = P.pot[4];
     if (a == 0) {
       const double g = A * exp(-be * x);
-      c[0] = g;
-      c[1] = -be * g;
-      c[2] = sgh * g;
-    } else {
+      if (part == 0) {
+        c[0] = g;
+        c[1] = -be * g;
+      } else {
+        c[2] = sgh * g;
+      }
+    } else if (part == 0) {
       const double em = exp(-aa * (x - re));
-      const double ep = exp(0.5 * be * x), en = exp(-0.5 * be * x);
       c[0] = sgh * Dm * (1.0 - em) * (1.0 - em);
       c[1] = 2.0 * Dm * (1.0 - em) * aa * em;
+    } else {
+      const double ep = exp(0.5 * be * x), en = exp(-0.5 * be * x);
       c[2] = ep + en;
       c[3] = 0.5 * be * (ep - en);
     }
   } else if (P.pot_kind == POT_HENON_HEILES) {
     const double lam = P.pot[0];
-    c[0] = x;
-    c[1] = sgh * (0.5 * x * x - (a >= 1 ? lam * x * x * x / 3.0 : 0.0));
-    c[2] = x * x;
-    c[3] = x - (a >= 1 ? lam * x * x : 0.0);
+    if (part == 0) {
+      c[0] = x;
+      c[1] = sgh * (0.5 * x * x - (a >= 1 ? lam * x * x * x / 3.0 : 0.0));
+    } else {
+      c[2] = x * x;
+      c[3] = x - (a >= 1 ? lam * x * x : 0.0);
+    }
   } else {  // SECREST_JOHNSON
     const double Dm = P.pot[0], be = P.pot[1], al = P.pot[2];
     if (a == 0) {
-      const double e1 = exp(-be * x), ea = exp(al * x);
-      c[0] = sgh * Dm * (1.0 - e1) * (1.0 - e1);
-      c[1] = 2.0 * Dm * (1.0 - e1) * be * e1;
-      c[2] = sgh * ea;
-      c[3] = al * ea;
-    } else {
+      if (part == 0) {
+        const double e1 = exp(-be * x);
+        c[0] = sgh * Dm * (1.0 - e1) * (1.0 - e1);
+        c[1] = 2.0 * Dm * (1.0 - e1) * be * e1;
+      } else {
+        const double ea = exp(al * x);
+        c[2] = sgh * ea;
+        c[3] = al * ea;
+      }
+    } else if (part == 0) {
       c[0] = exp(-al * x);
     }
   }
 }
-__device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, double sgh) {
+__device__ void vcolumns_eval(const Plan& P, int a, double x, double sgh, double* c) {
+  vcolumns_part(P, a, x, sgh, 0, c);
+  vcolumns_part(P, a, x, sgh, 1, c);
+}
+__device__ void vcolumns(const Plan& P, const Bufs& B, int e, int a, double x, double sgh, int part) {
   const int TT = P.tab_total;
   double c[NVCOL];
-  vcolumns_eval(P, a, x, sgh, c);
-#pragma unroll
-  for (int k = 0; k < NVCOL; ++k) __stcg(B.tabV + k * TT + e, c[k]);
+  vcolumns_part(P, a, x, sgh, part, c);
+  if (part == 0) {
+    __stcg(B.tabV + e, c[0]);
+    __stcg(B.tabV + TT + e, c[1]);
+    __stcg(B.tabV + 4 * TT + e, c[4]);
+  } else {
+    __stcg(B.tabV + 2 * TT + e, c[2]);
+    __stcg(B.tabV + 3 * TT + e, c[3]);
+  }
 }
 
-enum { TB_K = 1, TB_V = 2, TB_A = 4, TB_E = 8 };
+enum { TB_K = 1, TB_V = 2, TB_A = 4, TB_E = 8, TB_V1 = 16 /* second half of TB_V, build_tables only */ };
 
 // e^{i theta} for a table entry: FP64 for FP64 storage; for FP32 storage the
 // FP64 argument is reduced modulo 2 pi in FP64 and the sine and cosine are
@@ -596,9 +624,18 @@ __device__ double2 round_unit_f32(double x, double y, double m2) {
 // must follow before the tables are used.
 // Table entries of axis a, index j (c = j - N_a/2), from the CTA's scalars.
 // Kinetic factor K_a[j] = e^{(i/hbar)(delta_a p^K - tau minv_a (p^K)^2 / 2)}.
+// Exact 2^-k for n = 2^k (else 0): built from the exponent bits, no division.
+__device__ __forceinline__ double exact_inv_pow2(int n) {
+  if (n <= 0 || (n & (n - 1))) return 0.0;
+  return __hiloint2double((1023 - (31 - __clz(n))) << 20, 0);
+}
+// x / hbar, skipping the division (an FP64 subroutine on the critical path of
+// the table builds) when hbar = 1, where it is the identity.
+__device__ __forceinline__ double over_hbar(const Plan& P, double x) { return P.hbar == 1.0 ? x : x / P.hbar; }
+
 __device__ __forceinline__ double2 kin_entry(const Plan& P, const double* sc, const double2* sct, int a, double c) {
   const double pk = fma(c, P.dp[a], sc[SC_P + a]);
-  const double th = (sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk) / P.hbar;
+  const double th = over_hbar(P, sc[SC_DELTA + a] * pk - 0.5 * sc[SC_TAU] * P.minv[a] * pk * pk);
   double sn, cs;
   expi_prec(P.prec, th, sct, sn, cs);
   return P.prec ? round_unit_f32(cs, sn, 1.0) : make_double2(cs, sn);
@@ -607,27 +644,40 @@ __device__ __forceinline__ double2 kin_entry(const Plan& P, const double* sc, co
 __device__ __forceinline__ void demod_entry(const Plan& P, const double* sc, const double2* sct, int a, int j,
                                             double c, double2& A, double2& Ai) {
   const int n = P.ax[a].n;
-  const double th = -sc[SC_P + a] * c * P.dq[a] / P.hbar;
+  const double th = over_hbar(P, -sc[SC_P + a] * c * P.dq[a]);
   double sn, cs;
   expi_prec(P.prec, th, sct, sn, cs);
   const double sg = (j & 1) ? -1.0 : 1.0;
-  // conj(A)/N by division: a rounded 1/N would bias every inverse transform
+  // conj(A)/N by division: a rounded 1/N would bias every inverse transform.
+  // For N = 2^k the product with the exact 2^-k is the same number.
+  const double r = exact_inv_pow2(n);
+  double ax, ay;
+  if (r != 0.0) {
+    ax = sg * cs * r;
+    ay = -sg * sn * r;
+  } else {
+    ax = sg * cs / (double)n;
+    ay = -sg * sn / (double)n;
+  }
   if (P.prec) {
     A = round_unit_f32(sg * cs, sg * sn, 1.0);
     const double inv = 1.0 / ((double)n * (double)n);
-    Ai = round_unit_f32(sg * cs / (double)n, -sg * sn / (double)n, inv);
+    Ai = round_unit_f32(ax, ay, inv);
   } else {
     A = make_double2(sg * cs, sg * sn);
-    Ai = make_double2(sg * cs / (double)n, -sg * sn / (double)n);
+    Ai = make_double2(ax, ay);
   }
 }
 
 template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
   const int TT = P.tab_total, D = P.D;
   const int nch = (TT + 31) / 32;
-  int kinds[4], nk = 0;
+  int kinds[5], nk = 0;
+  if (what & TB_V) {  // the longest tasks first
+    kinds[nk++] = TB_V;
+    kinds[nk++] = TB_V1;
+  }
   if (what & TB_K) kinds[nk++] = TB_K;
-  if (what & TB_V) kinds[nk++] = TB_V;
   if (what & TB_A) kinds[nk++] = TB_A;
   if (what & TB_E) kinds[nk++] = TB_E;
   const int ntask = nk * nch;
@@ -649,8 +699,8 @@ template <typename V> __device__ void build_tables(const Plan& P, const Bufs& B,
       demod_entry(P, sc, S.sct, a, j, c, A, Ai);
       __stcg(B.tabA + e, A);
       __stcg(B.tabAi + e, Ai);
-    } else if (kind == TB_V) {
-      vcolumns(P, B, e, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH]);
+    } else if (kind == TB_V || kind == TB_V1) {
+      vcolumns(P, B, e, a, fma(c, P.dq[a], sc[SC_QN + a]), sc[SC_SGH], kind == TB_V1);
     } else {
       const double pk = fma(c, P.dp[a], sc[SC_P + a]);
       __stcg(B.tabE + e, 0.5 * P.minv[a] * pk * pk);
