@@ -171,6 +171,16 @@ def job_time_and_units(t_local, units_local, dist, device="cpu"):
     return float(t.item()), float(u.item())
 
 
+def headline_config(world):
+    """The workload of the headline line, shared by both arms."""
+    return {
+        "workload": "collinear atom-diatom, 256x256 moving grid, FP64 complex128, yoshida4 "
+                    "(3 TVT stages per step), dt = 1 a.u.",
+        "grid": list(N_GRID), "scheme": SCHEME, "stages_per_step": STAGES, "dt": DT,
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (one thread), same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -196,8 +206,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "collinear atom-diatom, 256x256 moving grid, FP64, yoshida4 dt=1 a.u.",
-                   "grid": list(N_GRID), "scheme": SCHEME, "dt": DT, "steps_per_iteration": 1},
+        "config": dict(headline_config(args.gpus), l2="not applicable: the CPU oracle"),
+        "time_steps_per_iteration": 1,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} time steps of the 256x256 workload, single thread"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -727,15 +737,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {
-            "workload": "collinear atom-diatom, 256x256 moving grid, FP64 complex128, yoshida4 "
-                        "(3 TVT stages per step), dt = 1 a.u.",
-            "grid": list(N_GRID), "scheme": SCHEME, "stages_per_step": STAGES, "dt": DT,
-            "time_steps_per_iteration": STEPS_PER_CALL,
-            "l2": "flushed (512 MB write) before every timed iteration; the 1 MB state is L2-resident "
-                  "within a call",
-            "parallelism": "replicas" if world > 1 else "single GPU",
-        },
+        "config": dict(headline_config(world),
+                       l2="flushed (512 MB write) before every timed iteration; the 1 MB state is "
+                          "L2-resident within a call"),
+        "time_steps_per_iteration": STEPS_PER_CALL,
         "error_vs_oracle": err,
         "roofline": {
             "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
