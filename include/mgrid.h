@@ -11,7 +11,7 @@
  * Substeps are composed symmetrically (eq:SO_TVT, eq:comp_TVT).
  *
  * Conventions shared by every entry point:
- *  - Grid: axis l has N_l points (even, 2 <= N_l <= 2048, only factors 2 and 3),
+ *  - Grid: axis l has N_l points (even, 2 <= N_l <= 1024, only factors 2 and 3),
  *    spacing dq_l > 0 and momentum spacing dp_l = 2 pi hbar / (N_l dq_l);
  *    x_l^J = q_l + (j_l - N_l/2) dq_l and p_l^K = p_l + (k_l - N_l/2) dp_l.
  *  - Arrays: row-major, last axis contiguous; complex values interleaved
