@@ -128,6 +128,25 @@ def test_fixed_grid_composition_order_vs_expm(scheme, order, dts, tol):
     assert min(errs) > 1e-12, errs
 
 
+def test_fixed_grid_suzuki_8_and_10_vs_expm():
+    # Suzuki 8 and 10 reach the roundoff floor before their slopes show; at
+    # dt = 0.25 each order gains at least two decades on the one below it
+    g = hh_grid_2d()
+    q, p = np.array([0.3, -0.2]), np.array([0.5, 0.1])
+    u0 = inputs.random_state(g.N, seed=5)
+    Tm, Vm = hamiltonian_matrix(g, q, p)
+    exact = expm(-1j * (Tm + Vm)) @ u0.ravel()
+    errs = {}
+    for scheme in ("suzuki6", "suzuki8", "suzuki10"):
+        g.set_u(u0)
+        g.set_state(g.get_state()[0], q, p)
+        g.set_u(u0)
+        g.propagate(4, 0.25, scheme, oracle.SPLIT_TVT, oracle.GRID_FIXED)
+        errs[scheme] = rel(g.get_u().ravel(), exact)
+    assert errs["suzuki8"] < 1e-9 and errs["suzuki10"] < 1e-11, errs
+    assert errs["suzuki8"] < 1e-2 * errs["suzuki6"] and errs["suzuki10"] < 1e-2 * errs["suzuki8"], errs
+
+
 # --------------------------------------------------------------------------
 # Moving grid vs closed-form Gaussian flows
 # --------------------------------------------------------------------------
