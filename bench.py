@@ -741,6 +741,7 @@ def main():
                        l2="flushed (512 MB write) before every timed iteration; the 1 MB state is "
                           "L2-resident within a call"),
         "time_steps_per_iteration": STEPS_PER_CALL,
+        "gp_stages_per_s": value * STAGES,
         "error_vs_oracle": err,
         "roofline": {
             "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
