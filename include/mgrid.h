@@ -181,6 +181,18 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
  * short-axis kernel off for that context. */
 int mg_propagate_path(const mg_ctx* ctx);
 
+/* Host-only planning query (no GPU, no context): the axis groups the
+ * short-axis kernel uses for a grid of D axes of lengths N in `precision`.
+ * Each group is a run of naxes[g] consecutive axes starting at first_axis[g],
+ * transformed together in one pass over the state (g = 0 is the group that
+ * ends at the last axis; a transform takes one pass per group).  Returns the
+ * number of groups, 0 if the grid does not take the short-axis kernel, -1 for
+ * an invalid grid.  first_axis and naxes: caller arrays of 8 ints (or NULL);
+ * threads, smem_bytes (or NULL): the CTA size and the dynamic shared memory
+ * of the cp.async layout (the TMA layout, chosen at mg_create, may differ). */
+int mg_short_axis_plan(int D, const int64_t* N, int precision, int* first_axis, int* naxes, int* threads,
+                       int* smem_bytes);
+
 /* <x> under the Morse ground state above (host quadrature helper for
  * choosing an initial grid centre). */
 double mg_morse_mean(double Dm, double a, double re, double mass, double hbar);

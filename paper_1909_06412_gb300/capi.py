@@ -24,7 +24,7 @@ MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON
 
 __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "MgError", "lib", "mg_workspace_bytes",
                                                         "mg_batch_workspace_bytes", "mg_morse_mean",
-                                                        "mg_propagate_noalloc"]
+                                                        "mg_propagate_noalloc", "mg_short_axis_plan"]
 
 _lib = None
 
@@ -54,6 +54,8 @@ def lib():
         L.mg_kernel_launches.restype = i64
         L.mg_propagate_path.argtypes = [vp]
         L.mg_propagate_path.restype = i32
+        L.mg_short_axis_plan.argtypes = [i32, vp, i32, vp, vp, vp, vp]
+        L.mg_short_axis_plan.restype = i32
         L.mg_morse_mean.argtypes = [d, d, d, d, d]
         L.mg_morse_mean.restype = d
         L.mg_status_string.argtypes = [i32]
@@ -100,6 +102,22 @@ def _f64(x, n=None):
 def mg_workspace_bytes(N, precision=MG_FP64):
     n = np.ascontiguousarray(N, dtype=np.int64)
     return int(lib().mg_workspace_bytes(len(n), _ptr(n), precision))
+
+
+def mg_short_axis_plan(N, precision=MG_FP64):
+    """Host-only: the short-axis kernel's axis groups for a grid of axis
+    lengths N, as (first_axis, naxes) pairs, with the CTA size and dynamic
+    shared memory; None if the grid does not take that kernel."""
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    first, nax = np.zeros(8, dtype=np.int32), np.zeros(8, dtype=np.int32)
+    thr, smem = np.zeros(1, dtype=np.int32), np.zeros(1, dtype=np.int32)
+    ng = lib().mg_short_axis_plan(n.size, _ptr(n), precision, _ptr(first), _ptr(nax), _ptr(thr), _ptr(smem))
+    if ng < 0:
+        raise MgError(MG_ERR_ARG, "mg_short_axis_plan")
+    if ng == 0:
+        return None
+    return {"groups": [(int(first[g]), int(nax[g])) for g in range(ng)], "threads": int(thr[0]),
+            "smem_bytes": int(smem[0])}
 
 
 def mg_morse_mean(Dm, a, re, mass, hbar=1.0):

@@ -1169,6 +1169,43 @@ int mg_propagate_path(const mg_ctx* c) {
   return c->SP.tma ? 2 : 1;
 }
 
+int mg_short_axis_plan(int D, const int64_t* N, int precision, int* first_axis, int* naxes, int* threads,
+                       int* smem_bytes) {
+  if (!N || D < 1 || D > MAXD || (precision != MG_FP64 && precision != MG_FP32_MIXED)) return -1;
+  for (int l = 0; l < D; ++l)
+    if (!axis_supported(N[l])) return -1;
+  // the parts of the grid plan that the short-axis planner reads (as mg_create
+  // fills them)
+  Plan P;
+  std::memset(&P, 0, sizeof(Plan));
+  P.D = D;
+  P.prec = precision;
+  P.hbar = 1.0;
+  P.npts = 1;
+  for (int l = 0; l < D; ++l) P.npts *= N[l];
+  for (int l = D - 1; l >= 0; --l) {
+    P.ax[l].n = (int)N[l];
+    P.ax[l].stride = (l == D - 1) ? 1 : P.ax[l + 1].stride * N[l + 1];
+  }
+  for (int l = 0; l < D; ++l) {
+    P.N[l] = N[l];
+    P.dq[l] = 1.0;
+    P.ax[l].outer = P.npts / (P.ax[l].n * P.ax[l].stride);
+    P.ax[l].toff = P.tab_total;
+    P.tab_total += P.ax[l].n;
+    P.maxn = std::max(P.maxn, P.ax[l].n);
+  }
+  ShortPlan SP;
+  if (!short_plan(P, SP)) return 0;
+  for (int g = 0; g < SP.ngroups; ++g) {
+    if (first_axis) first_axis[g] = SP.grp[g].l0;
+    if (naxes) naxes[g] = SP.grp[g].g;
+  }
+  if (threads) *threads = SP.threads;
+  if (smem_bytes) *smem_bytes = SP.smem_bytes;
+  return SP.ngroups;
+}
+
 const char* mg_status_string(int s) {
   switch (s) {
     case MG_OK: return "ok";
