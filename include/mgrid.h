@@ -181,6 +181,15 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
  * short-axis kernel off for that context. */
 int mg_propagate_path(const mg_ctx* ctx);
 
+/* Host-only (no GPU): the stage coefficients gamma_1..gamma_S of a named
+ * composition (eq:comp_TVT), each stage a second-order step of length
+ * gamma_k dt.  Triple jump (Yoshida): S_{2k+2}(h) = S_{2k}(a h) S_{2k}((1-2a) h)
+ * S_{2k}(a h), a = 1/(2 - 2^{1/(2k+1)}); Suzuki fractal: S_{2k}(a h)^2
+ * S_{2k}((1-4a) h) S_{2k}(a h)^2, a = 1/(4 - 4^{1/(2k+1)}).  Writes at most
+ * `max` values to gamma (may be NULL) and returns S, or -1 for an unknown
+ * name. */
+int mg_scheme_coefficients(const char* scheme, double* gamma, int max);
+
 /* Host-only planning query (no GPU, no context): the axis groups the
  * short-axis kernel uses for a grid of D axes of lengths N in `precision`.
  * Each group is a run of naxes[g] consecutive axes starting at first_axis[g],

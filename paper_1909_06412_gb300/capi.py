@@ -24,7 +24,8 @@ MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON
 
 __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "MgError", "lib", "mg_workspace_bytes",
                                                         "mg_batch_workspace_bytes", "mg_morse_mean",
-                                                        "mg_propagate_noalloc", "mg_short_axis_plan"]
+                                                        "mg_propagate_noalloc", "mg_short_axis_plan",
+                                                        "mg_scheme_coefficients"]
 
 _lib = None
 
@@ -56,6 +57,8 @@ def lib():
         L.mg_propagate_path.restype = i32
         L.mg_short_axis_plan.argtypes = [i32, vp, i32, vp, vp, vp, vp]
         L.mg_short_axis_plan.restype = i32
+        L.mg_scheme_coefficients.argtypes = [ctypes.c_char_p, vp, i32]
+        L.mg_scheme_coefficients.restype = i32
         L.mg_morse_mean.argtypes = [d, d, d, d, d]
         L.mg_morse_mean.restype = d
         L.mg_status_string.argtypes = [i32]
@@ -102,6 +105,16 @@ def _f64(x, n=None):
 def mg_workspace_bytes(N, precision=MG_FP64):
     n = np.ascontiguousarray(N, dtype=np.int64)
     return int(lib().mg_workspace_bytes(len(n), _ptr(n), precision))
+
+
+def mg_scheme_coefficients(scheme):
+    """Host-only: the stage coefficients gamma_k of a named composition."""
+    S = lib().mg_scheme_coefficients(scheme.encode(), None, 0)
+    if S < 0:
+        raise MgError(MG_ERR_ARG, "mg_scheme_coefficients")
+    g = np.zeros(S)
+    lib().mg_scheme_coefficients(scheme.encode(), _ptr(g), S)
+    return g
 
 
 def mg_short_axis_plan(N, precision=MG_FP64):

@@ -1169,6 +1169,14 @@ int mg_propagate_path(const mg_ctx* c) {
   return c->SP.tma ? 2 : 1;
 }
 
+int mg_scheme_coefficients(const char* scheme, double* gamma, int max) {
+  std::vector<double> g;
+  if (!scheme_coeffs(scheme, g)) return -1;
+  if (gamma)
+    for (int i = 0; i < (int)g.size() && i < max; ++i) gamma[i] = g[i];
+  return (int)g.size();
+}
+
 int mg_short_axis_plan(int D, const int64_t* N, int precision, int* first_axis, int* naxes, int* threads,
                        int* smem_bytes) {
   if (!N || D < 1 || D > MAXD || (precision != MG_FP64 && precision != MG_FP32_MIXED)) return -1;
