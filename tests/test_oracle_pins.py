@@ -362,6 +362,29 @@ def test_composition_coefficients(name, stages, gmax):
         assert abs(np.sum(g ** pw)) < 1e-10
 
 
+@pytest.mark.parametrize("kind,D,params", [
+    (oracle.POT_HARMONIC, 3, list(np.array(inputs.DUSCHINSKY3D["K"]).ravel()) + [0.3, -0.2, 0.1]),
+    (oracle.POT_ATOM_DIATOM, 2, [inputs.ATOM_DIATOM[k] for k in ("Dm", "a", "re", "A", "beta")]),
+    (oracle.POT_HENON_HEILES, 8, [inputs.HENON_HEILES["lam"]]),
+    (oracle.POT_SECREST_JOHNSON, 2, [0.17, 1.0, 1.8])])
+def test_potential_gradient_matches_finite_differences(kind, D, params):
+    # the Ehrenfest force <dV/dq> moves the p-centre (eq:eom_pt_solution_case_III_V);
+    # the oracle's analytic gradient against central differences of its V
+    g = oracle.Grid((4,) * D, (0.5,) * D)
+    g.set_potential(kind, params)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1.5, 1.5, size=(16, D))
+    if kind == oracle.POT_ATOM_DIATOM:
+        x += np.array([3.0, 1.4])  # R beyond the wall's steepest part, r near re
+    V, grad = g.potential(x)
+    h = 1e-5
+    for a in range(D):
+        e = np.zeros(D)
+        e[a] = h
+        fd = (g.potential(x + e)[0] - g.potential(x - e)[0]) / (2 * h)
+        assert np.allclose(grad[:, a], fd, rtol=1e-7, atol=1e-8 * np.abs(V).max()), (a, grad[:, a], fd)
+
+
 def test_morse_mean_closed_form():
     P = inputs.ATOM_DIATOM
     m = P["mu"][1]
