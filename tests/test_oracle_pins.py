@@ -316,6 +316,43 @@ def test_initial_energy_of_the_harmonic_model():
     assert abs(duschinsky(-0.017).observables()[1] - E0) > 1.0
 
 
+def test_initial_energy_of_the_atom_diatom_state():
+    # Sec. III.B model on the 256 x 256 grid: a Gaussian in R (eq:general_GWP)
+    # times the Morse ground state in r.  Closed forms: <T_R> = (p0^2 +
+    # 1/(2 sigma^2)) / (2 mu_R); the Morse ground state's <T_r + V_Morse> =
+    # hbar w/2 - (hbar w)^2/(16 D), w = a sqrt(2 D / mu_r); the two exponential
+    # terms factor into <e^{-beta R}> = e^{-beta R0 + beta^2 sigma^2/4} times
+    # <e^{+-beta r/2}> by quadrature of the Morse density z^(2 lam - 1) e^-z.
+    from scipy.integrate import quad
+
+    P = inputs.ATOM_DIATOM
+    Dm, a, re, A, be = (P[k] for k in ("Dm", "a", "re", "A", "beta"))
+    muR, mur = P["mu"]
+    R0, P0, sg = P["R0"], P["P0"], P["sigma"]
+    lam = np.sqrt(2 * mur * Dm) / a
+    w = a * np.sqrt(2 * Dm / mur)
+    morse = w / 2 - w ** 2 / (16 * Dm)
+    TR = (P0 ** 2 + 1 / (2 * sg ** 2)) / (2 * muR)
+
+    def dens(r):
+        z = 2 * lam * np.exp(-a * (r - re))
+        return np.exp((2 * lam - 1) * np.log(z) - z)
+
+    kw = dict(limit=400, epsabs=0, epsrel=1e-13)
+    nrm = quad(dens, re - 2.5, re + 6, **kw)[0]
+    ex = sum(quad(lambda r, s=s: dens(r) * np.exp(s * be * r / 2), re - 2.5, re + 6, **kw)[0] for s in (1, -1))
+    E = TR + morse + A * np.exp(-be * R0 + be ** 2 * sg ** 2 / 4) * ex / nrm
+
+    g = oracle.Grid(P["N"], P["dq"], minv=(1 / muR, 1 / mur))
+    g.set_potential(oracle.POT_ATOM_DIATOM, [Dm, a, re, A, be])
+    rbar = oracle.morse_mean(Dm, a, re, mur)
+    g.set_separable([("gauss", R0, P0, sg), ("morse", Dm, a, re, mur)], [R0, rbar], [P0, 0.0])
+    n, Eo, mq, mp = g.observables()
+    assert abs(n - 1) < 1e-13
+    assert abs(Eo - E) < 1e-12 * E
+    assert np.allclose(mq, [R0, rbar], rtol=0, atol=1e-12) and np.allclose(mp, [P0, 0.0], rtol=0, atol=1e-12)
+
+
 def test_overlap_harmonic_displaced_ground_state():
     # Fig. 4 caption: phi0 = psi0 displaced by (-1, 1, 1) has <psi0|phi0> = 0.472.
     P = inputs.DUSCHINSKY3D
