@@ -353,6 +353,21 @@ def test_initial_energy_of_the_atom_diatom_state():
     assert np.allclose(mq, [R0, rbar], rtol=0, atol=1e-12) and np.allclose(mp, [P0, 0.0], rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("D,N", [(2, 64), (3, 32)])
+def test_initial_energy_of_the_henon_heiles_state(D, N):
+    # Sec. III.C model: a unit-width Gaussian at q = 2 in every coordinate has
+    # <q> = 2, var 1/2, <q^2> = 9/2, <q^3> = 11, <p^2> = 1/2 per coordinate, so
+    # E = D/4 + 9D/4 + lambda (D-1) (<q^2><q> - <q^3>/3) = 5D/2 + lambda (D-1) 16/3
+    lam = inputs.HENON_HEILES["lam"]
+    dq = np.sqrt(2 * np.pi / N)
+    g = oracle.Grid((N,) * D, (dq,) * D)
+    g.set_potential(oracle.POT_HENON_HEILES, [lam])
+    g.set_separable([("gauss", 2.0, 0.0, 1.0)] * D, [2.0] * D, [0.0] * D)
+    n, E, mq, mp = g.observables()
+    exact = 2.5 * D + lam * (D - 1) * 16.0 / 3.0
+    assert abs(n - 1) < 1e-13 and abs(E - exact) < 1e-13 * exact, (E, exact)
+
+
 def test_overlap_harmonic_displaced_ground_state():
     # Fig. 4 caption: phi0 = psi0 displaced by (-1, 1, 1) has <psi0|phi0> = 0.472.
     P = inputs.DUSCHINSKY3D
