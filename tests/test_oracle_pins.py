@@ -110,6 +110,23 @@ def test_fixed_grid_kinetic_substep_is_matrix_exponential():
     ("suzuki6", 6, [0.25, 0.125, 0.0625], 0.5), ("yoshida8", 8, [0.125, 0.0625, 0.03125], 0.5),
     ("yoshida10", 10, [0.125, 0.0625, 0.03125], 0.5)])
 def test_fixed_grid_composition_order_vs_expm(scheme, order, dts, tol):
+    composition_order_vs_expm(scheme, order, dts, tol, oracle.SPLIT_TVT)
+
+
+# VTV (T and V exchanged in every stage, eq:SO_TVT) has the same orders; a
+# stage in the wrong order (e.g. V(h) T(h/2) ...) is not symmetric and drops
+# to first order.  The first-order TV split of eq:SO_TV converges with slope 1.
+@pytest.mark.parametrize("scheme,order,dts,tol,split", [
+    ("strang", 2, [0.25, 0.125, 0.0625], 0.35, oracle.SPLIT_VTV),
+    ("yoshida4", 4, [0.125, 0.0625, 0.03125], 0.35, oracle.SPLIT_VTV),
+    ("yoshida6", 6, [0.125, 0.0625, 0.03125], 0.35, oracle.SPLIT_VTV),
+    ("suzuki4", 4, [0.125, 0.0625, 0.03125], 0.35, oracle.SPLIT_VTV),
+    ("strang", 1, [0.05, 0.025, 0.0125], 0.15, oracle.SPLIT_TV)])
+def test_fixed_grid_vtv_and_tv_orders_vs_expm(scheme, order, dts, tol, split):
+    composition_order_vs_expm(scheme, order, dts, tol, split)
+
+
+def composition_order_vs_expm(scheme, order, dts, tol, split):
     g = hh_grid_2d()
     q, p = np.array([0.3, -0.2]), np.array([0.5, 0.1])
     u0 = inputs.random_state(g.N, seed=5)
@@ -121,7 +138,7 @@ def test_fixed_grid_composition_order_vs_expm(scheme, order, dts, tol):
         g.set_u(u0)
         g.set_state(g.get_state()[0], q, p)
         g.set_u(u0)
-        g.propagate(round(t / dt), dt, scheme, oracle.SPLIT_TVT, oracle.GRID_FIXED)
+        g.propagate(round(t / dt), dt, scheme, split, oracle.GRID_FIXED)
         errs.append(rel(g.get_u().ravel(), exact))
     slopes = np.diff(np.log(errs)) / np.diff(np.log(dts))
     assert np.all(np.abs(slopes - order) < tol), (errs, slopes)
@@ -164,15 +181,23 @@ def run_split_gaussians(gs, ms, ks, cs, dt, steps, gammas):
                 G.kinetic(h / 2, m)
 
 
+# Both readings of the kinetic substep's centre motion: the <p> reduction
+# (eq:eom_qt_case_III_T) and the p-centre itself (eq:eom_qt_solution_case_III_T).
+# For a Gaussian the two coincide: the p-centre and the packet's momentum
+# receive the same kicks -tau k (x_c - c) in every potential substep and start
+# equal, so either way the grid centre must follow the packet's centre
+# (position Verlet, Sec. II.H).  A wrong branch (other momentum, sign, mass)
+# moves the grid away from the packet and fails both checks.
 @pytest.mark.parametrize("scheme", ["strang", "yoshida4"])
-def test_moving_grid_matches_discrete_gaussian_closed_form(scheme):
+@pytest.mark.parametrize("motion", [oracle.GRID_ADAPTIVE, oracle.GRID_ADAPTIVE_CENTRE_P])
+def test_moving_grid_matches_discrete_gaussian_closed_form(scheme, motion):
     # 1D, omega = 1, spacing 0.3, 64 points: the packet is < 1e-20 at the edges.
     N, dq, dt, steps = (64,), (0.3,), 0.01, 1000 if scheme == "strang" else 300
     q0, p0 = 1.0, 0.5
     g = oracle.Grid(N, dq)
     g.set_potential(oracle.POT_HARMONIC, [1.0, 0.0])
     g.set_separable([("gauss", q0, p0, 1.0)], [q0], [p0])
-    g.propagate(steps, dt, scheme)
+    g.propagate(steps, dt, scheme, oracle.SPLIT_TVT, motion)
     psi, q, p, t = g.get_state()
     G = Gauss1D(q0, p0, 1.0)
     run_split_gaussians([G], [1.0], [1.0], [0.0], dt, steps, oracle.scheme(scheme))
@@ -183,7 +208,8 @@ def test_moving_grid_matches_discrete_gaussian_closed_form(scheme):
     assert abs(t - steps * dt) < 1e-9
 
 
-def test_moving_grid_2d_mass_hbar_and_centre_closed_form():
+@pytest.mark.parametrize("motion", [oracle.GRID_ADAPTIVE, oracle.GRID_ADAPTIVE_CENTRE_P])
+def test_moving_grid_2d_mass_hbar_and_centre_closed_form(motion):
     hbar = 0.7
     minv = np.array([0.5, 2.0])
     k = np.array([1.3, 0.6])
@@ -191,12 +217,12 @@ def test_moving_grid_2d_mass_hbar_and_centre_closed_form():
     q0, p0 = np.array([1.1, -0.4]), np.array([0.3, 0.6])
     omega = np.sqrt(k * minv)
     sig = np.sqrt(hbar / (omega / minv))  # sigma^2 = hbar/(m omega)
-    N, dq = (48, 96), (0.25, 0.22)
+    N, dq = (64, 128), (0.25, 0.22)
     g = oracle.Grid(N, dq, minv=minv, hbar=hbar)
     g.set_potential(oracle.POT_HARMONIC, list(np.diag(k).ravel()) + list(c))
     g.set_separable([("gauss", q0[l], p0[l], sig[l]) for l in range(2)], q0, p0)
     dt, steps = 0.02, 200
-    g.propagate(steps, dt, "yoshida4")
+    g.propagate(steps, dt, "yoshida4", oracle.SPLIT_TVT, motion)
     psi, q, p, _ = g.get_state()
     gs = [Gauss1D(q0[l], p0[l], sig[l], hbar) for l in range(2)]
     run_split_gaussians(gs, 1 / minv, k, c, dt, steps, oracle.scheme("yoshida4"))
@@ -351,6 +377,36 @@ def test_initial_energy_of_the_atom_diatom_state():
     assert abs(n - 1) < 1e-13
     assert abs(Eo - E) < 1e-12 * E
     assert np.allclose(mq, [R0, rbar], rtol=0, atol=1e-12) and np.allclose(mp, [P0, 0.0], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("q0,p0,sig,minv", [
+    ((0.0, 24.0), (0.0, -3.56), (1.0, np.sqrt(8.0)), (1.0, 1.5)),
+    ((0.4, 21.0), (0.7, -3.0), (0.8, 2.5), (0.7, 1.2))])
+def test_initial_energy_of_the_secrest_johnson_state(q0, p0, sig, minv):
+    # eq:modified_secrest_johnson, V = D (1 - e^{-beta q1})^2 + e^{-alpha (q2 - q1)},
+    # with D = 20, beta = 0.158, alpha = 0.3 (Sec. III.B), under a product of
+    # Gaussians of eq:general_GWP.  |psi|^2 is normal with mean q0_l and
+    # variance sigma_l^2 / 2 per axis, so <e^{c q_l}> = e^{c q0_l + c^2 sigma_l^2 / 4}
+    # and <V> = D (1 - 2 <e^{-beta q1}> + <e^{-2 beta q1}>) + <e^{-alpha q2}> <e^{alpha q1}>;
+    # <T> = sum_l minv_l (p0_l^2 + hbar^2 / (2 sigma_l^2)) / 2.  A sign of alpha,
+    # an exchange of q1 and q2 or a dropped factor changes E by far more than
+    # the tolerance.
+    Dm, be, al = 20.0, 0.158, 0.3
+    q0, p0, sig, minv = (np.array(v, dtype=float) for v in (q0, p0, sig, minv))
+
+    def mexp(c, l):
+        return np.exp(c * q0[l] + c * c * sig[l] ** 2 / 4)
+
+    V = Dm * (1 - 2 * mexp(-be, 0) + mexp(-2 * be, 0)) + mexp(-al, 1) * mexp(al, 0)
+    T = np.sum(minv * (p0 ** 2 + 1 / (2 * sig ** 2))) / 2
+    N, dq = (64, 64), (28.0 / 64, 48.0 / 64)
+    g = oracle.Grid(N, dq, minv=minv)
+    g.set_potential(oracle.POT_SECREST_JOHNSON, [Dm, be, al])
+    g.set_separable([("gauss", q0[l], p0[l], sig[l]) for l in range(2)], q0, p0)
+    n, E, mq, mp = g.observables()
+    assert abs(n - 1) < 1e-13
+    assert abs(E - (T + V)) < 1e-12 * (T + V), (E, T + V)
+    assert np.allclose(mq, q0, rtol=0, atol=1e-12) and np.allclose(mp, p0, rtol=0, atol=1e-12)
 
 
 @pytest.mark.parametrize("D,N", [(2, 64), (3, 32)])
