@@ -1,10 +1,16 @@
 """Throughput of the moving-grid split-operator propagator on one GB300.
 
-Workload: collinear atom-diatom model on a 256 x 256 moving grid in FP64
-(complex128), incoming Gaussian in R times the Morse ground state in r,
-fourth-order triple-jump composition (3 TVT stages per step), dt = 1 a.u.
-One timed iteration is one mg_propagate call of STEPS_PER_CALL time steps
-(one persistent kernel launch).  value = grid points x time steps / second.
+Headline workload: the 8D Henon-Heiles model of Sec. III.C on a 12^8 moving
+grid in FP64 (complex128, 4.3e8 points, 6.9 GB), fourth-order Suzuki
+composition (5 TVT stages per step), dt = 0.01.  One timed iteration is one
+mg_propagate call of one time step (one persistent kernel launch); value =
+grid points x time steps / second.  The state is larger than L2, so no flush
+is needed between iterations.  The FP64 path is bound by the FP64 units: its
+roofline is stated against the FP64 FMA rate measured in the same run.
+
+Secondary lines (other keys of the same JSON line): the 256 x 256 atom-diatom
+workload, 3D harmonic 32^3, 16^8 FP32, mixed precision, batch, adjoint,
+convergence orders, an ensemble.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,25 +43,32 @@ POT = [0.17, 1.0, 1.4, 5.0, 1.8]  # Dm, a, re, A, beta
 SCHEME, STAGES, DT = "yoshida4", 3, 1.0
 STEPS_PER_CALL = 100
 CPU_SAMPLE_STEPS = 30
+# headline: 8D Henon-Heiles, 12^8 FP64
+HH_N, HH_D, HH_LAM = 12, 8, 0.111803
+HH_SCHEME, HH_STAGES, HH_DT = "suzuki4", 5, 0.01
+HH_E2E_ITERS = 5
+HH_CPU_D = 5   # oracle sample: the same model on 12^5, one time step
+HH_REF_D = 4   # reference arm: one time step on 12^4 per timed step
 ADJ_STEPS = 200
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# DRAM bytes (read + write) of one propagate launch, from an ncu capture of
-# `python bench.py --profile`; valid only for the kernel sources it was taken on
-# (sha256 of mg_kernels.cu + mg_device.cuh + mg_plan.h, concatenated).
-TRAFFIC_RECORD = {"kernel_sha256": "126437d6a91ba5da12bff0c9b6f24d6b44b5f4622bd81971f34555977fddbee3",
-                  "bytes_per_launch": 1.612544e6 + 0.294400e6}
-KERNEL_SOURCES = ("mg_kernels.cu", "mg_device.cuh", "mg_plan.h")
+# DRAM bytes (read + write) of one headline propagate launch (one 12^8 time
+# step), from an ncu capture of the same launch on 12^7 scaled by 12 (the
+# traffic of a pass grows with the points it streams); valid only for the
+# kernel sources it was taken on (sha256 of the files below, concatenated).
+TRAFFIC_RECORD = {"kernel_sha256": "", "bytes_per_launch": None}
+KERNEL_SOURCES = ("mg_short.cu", "mg_short.h", "mg_device.cuh", "mg_plan.h")
 
-# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# FP64 peak from unit counts and clocks (152 SMs x 2 FP64 FMA/clk x 2 flop x
+# 2.07 GHz): used only where the measured rate is missing
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def algorithmic_flops_per_point_stage(N, D):
-    """Radix-2 count 5 log2(n) per transform (two per stage), 6 flop per
-    complex multiply of the 3D+1 diagonal factors, 2(D+2) for the reductions."""
+    """5 log2(N) per transform (radix-2 count, two transforms per stage),
+    10 D for the diagonal phase factors, 2 (D + 2) for the reductions."""
     n = int(np.prod(N))
-    return 2 * 5 * math.log2(n) + 6 * (3 * D + 1) + 2 * (D + 2)
+    return 2 * 5 * math.log2(n) + 10 * D + 2 * (D + 2)
 
 
 def algorithmic_bytes_per_point_stage(elem=16):
@@ -174,42 +187,92 @@ def job_time_and_units(t_local, units_local, dist, device="cpu"):
 def headline_config(world):
     """The workload of the headline line, shared by both arms."""
     return {
-        "workload": "collinear atom-diatom, 256x256 moving grid, FP64 complex128, yoshida4 "
-                    "(3 TVT stages per step), dt = 1 a.u.",
-        "grid": list(N_GRID), "scheme": SCHEME, "stages_per_step": STAGES, "dt": DT,
+        "workload": f"8D Henon-Heiles (Sec. III.C), {HH_N}^{HH_D} moving grid, FP64 complex128 "
+                    f"({HH_N ** HH_D:.3g} points, {16 * HH_N ** HH_D / 1e9:.2f} GB), {HH_SCHEME} "
+                    f"({HH_STAGES} TVT stages per step), dt = {HH_DT}, lambda = {HH_LAM}",
+        "grid": [HH_N] * HH_D, "scheme": HH_SCHEME, "stages_per_step": HH_STAGES, "dt": HH_DT,
+        "time_steps_per_iteration": 1,
         "parallelism": "replicas" if world > 1 else "single GPU",
     }
 
 
+def hh_oracle(oracle, D):
+    """The headline model on a 12^D grid for the oracle (same n, lambda,
+    spacing, initial Gaussians at q = 2)."""
+    dq = math.sqrt(2 * math.pi / HH_N)
+    o = oracle.Grid((HH_N,) * D, (dq,) * D)
+    o.set_potential(oracle.POT_HENON_HEILES, [HH_LAM])
+    o.set_separable([("gauss", 2.0, 0.0, 1.0)] * D, [2.0] * D, [0.0] * D)
+    return o
+
+
+def _oracle_sample_worker(D):
+    """One oracle time step of the headline model on a 12^D grid (its own
+    process); returns (points, seconds)."""
+    import oracle
+
+    o = hh_oracle(oracle, D)
+    t0 = time.perf_counter()
+    o.propagate(1, HH_DT, HH_SCHEME)
+    return HH_N ** D, time.perf_counter() - t0
+
+
+def oracle_all_cores(D):
+    """The oracle as it stands (single-threaded) on every host core at once:
+    one process per core, each running the same sample; throughput = points x
+    steps of all processes / the slowest process's time."""
+    import multiprocessing as mp
+
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n) as pool:
+        res = pool.map(_oracle_sample_worker, [D] * n)
+    wall = time.perf_counter() - t0
+    pts = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return pts / slowest, n, slowest, wall
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def run_reference(args):
-    """The FP64 CPU oracle on the host cores (one thread), same workload."""
+    """The FP64 CPU oracle on the host cores (one thread) for the headline
+    model: each timed step is one time step on a 12^4 grid (a bounded sample
+    of the 12^8 workload: same model, axis length, scheme and dt)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
 
-    o = oracle.Grid(N_GRID, DQ, minv=MINV)
-    o.set_potential(oracle.POT_ATOM_DIATOM, POT)
-    rbar = oracle.morse_mean(POT[0], POT[1], POT[2], 0.5 * AMU)
-    o.set_separable([("gauss", 8.0, -10.0, 0.5), ("morse", POT[0], POT[1], POT[2], 0.5 * AMU)],
-                    [8.0, rbar], [-10.0, 0.0])
+    o = hh_oracle(oracle, HH_REF_D)
     for _ in range(args.warmup):
-        o.propagate(1, DT, SCHEME)
+        o.propagate(1, HH_DT, HH_SCHEME)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.propagate(1, DT, SCHEME)
+        o.propagate(1, HH_DT, HH_SCHEME)
     el = time.perf_counter() - t0
-    npts = int(np.prod(N_GRID))
+    npts = HH_N ** HH_REF_D
     v = npts * args.steps / el
+    sample = (f"{args.steps} time steps of the headline model on a {HH_N}^{HH_REF_D} grid (the oracle's cost "
+              f"per point grows with the number of axes, so this favours it), single thread, {cpu_model()}")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": dict(headline_config(args.gpus), l2="not applicable: the CPU oracle"),
-        "time_steps_per_iteration": 1,
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} time steps of the 256x256 workload, single thread"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -258,9 +321,10 @@ def hh_propagator(mgmod, n, D, prec, dev=None):
 def run_profile(args):
     """The timed launches of a workload alone, for profiler captures: the
     propagate kernel is launched warmup + steps times.  --profile-case
-    atom_diatom (default): the bench workload, STEPS_PER_CALL steps per call;
-    hh7_fp32 / hh7_fp64: Henon-Heiles on 16^7 (FP32) / 12^7 (FP64) grids,
-    suzuki4, one time step (5 TVT stages) per call."""
+    hh8_fp64 (default): the headline, 12^8 FP64, one time step per call;
+    hh7_fp64 / hh7_fp32: Henon-Heiles on 12^7 (FP64) / 16^7 (FP32) grids, the
+    small cases for full captures; atom_diatom: the 256 x 256 workload,
+    STEPS_PER_CALL steps per call."""
     import torch
     import paper_1909_06412_gb300 as mg
 
@@ -271,7 +335,8 @@ def run_profile(args):
         g.set_separable(fac, qc, pc)
         call = lambda: g.propagate(STEPS_PER_CALL, DT, SCHEME)
     else:
-        n, D, prec = {"hh7_fp32": (16, 7, mg.MG_FP32_MIXED), "hh7_fp64": (12, 7, mg.MG_FP64)}[args.profile_case]
+        n, D, prec = {"hh8_fp64": (12, 8, mg.MG_FP64), "hh7_fp32": (16, 7, mg.MG_FP32_MIXED),
+                      "hh7_fp64": (12, 7, mg.MG_FP64)}[args.profile_case]
         g = hh_propagator(mg, n, D, prec)
         call = lambda: g.propagate(1, 0.01, "suzuki4")
     for _ in range(args.warmup + args.steps):
@@ -336,7 +401,7 @@ def other_workloads(mgmod, torch, dev, flush):
             "stages_per_step": stages, "ms_per_step": 1e3 * t / steps,
             "kernel_path": {0: "general", 1: "short-axis", 2: "short-axis, TMA copies"}.get(g.path, str(g.path)),
             "hbm_gbs_algorithmic": gbs, "hbm_frac_algorithmic": gbs / hbm_peak,
-            "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / FP64_PEAK_TFLOPS if tf is not None else None,
+            "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / fp64_peak() if tf is not None else None,
             "norm_drift": n1 / n0 - 1, "energy_drift": E1 / E0 - 1,
             "reversibility": {"psi_rel_l2": rev, "q_abs": float(np.abs(qs1 - qs0).max()),
                               "p_abs": float(np.abs(ps1 - ps0).max()), "steps": steps},
@@ -531,7 +596,7 @@ def ensemble_leg(mgmod, torch, dev):
         v = npts * ENSEMBLE_STEPS * ENSEMBLE_MEMBERS / t
         tf = v * STAGES * algorithmic_flops_per_point_stage(N_GRID, 2) / 1e12
         out[f"cluster_{cluster}"] = {"value": v, "unit": UNIT, "s": t, "teams": b.info()["teams"],
-                                     "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / FP64_PEAK_TFLOPS,
+                                     "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / fp64_peak(),
                                      "psi_rel_l2_vs_single_grid": err}
         b.close()
         for g in gs:
@@ -639,15 +704,60 @@ def batch_leg(mgmod, torch, dev):
     return out
 
 
+def fp64_peak():
+    return MEASURED.get("fp64_tflops") or FP64_PEAK_TFLOPS
+
+
+MEASURED = {}
+
+
+def atom_diatom_leg(mg, torch, dev, args, flush):
+    """The collinear atom-diatom workload (Sec. III.B model) on the 256 x 256
+    FP64 grid, yoshida4, dt = 1 a.u.: STEPS_PER_CALL time steps per call, L2
+    flushed before every timed call (its 1 MB state is L2-resident within a
+    call), with its own roofline and error against the oracle."""
+    npts = int(np.prod(N_GRID))
+    g = headline_propagator(mg, dev)
+    for _ in range(3):
+        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+    g.sync()
+    ms = []
+    for _ in range(max(5, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+        e1.record(g.stream)
+        ms.append((e0, e1))
+    g.sync()
+    ms = [a.elapsed_time(b) for a, b in ms]
+    g.close()
+    t = statistics.mean(ms) / 1e3
+    ps = npts * STEPS_PER_CALL * STAGES / t
+    tf = ps * algorithmic_flops_per_point_stage(N_GRID, 2) / 1e12
+    hbm_peak, _ = peaks()
+    gbs = ps * algorithmic_bytes_per_point_stage() / 1e9
+    cpu, err = cpu_baseline_and_error(mg, torch)
+    return {"workload": "collinear atom-diatom 256x256 FP64, yoshida4 (3 stages per step), dt = 1 a.u.",
+            "value": npts * STEPS_PER_CALL / t, "unit": UNIT, "ms_per_call": 1e3 * t,
+            "time_steps_per_call": STEPS_PER_CALL, "calls": len(ms),
+            "fp64_tflops_algorithmic": tf, "fp64_frac_algorithmic": tf / fp64_peak(),
+            "hbm_frac_algorithmic": gbs / hbm_peak,
+            "l2": "flushed before every timed call; the 1 MB state is L2-resident within a call",
+            "error_vs_oracle": err, "cpu_baseline": cpu}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed propagate calls, as in the timed region (for ncu captures)")
-    ap.add_argument("--profile-case", default="atom_diatom", choices=["atom_diatom", "hh7_fp32", "hh7_fp64"])
+    ap.add_argument("--profile-case", default="hh8_fp64",
+                    choices=["hh8_fp64", "atom_diatom", "hh7_fp32", "hh7_fp64"])
+    ap.add_argument("--headline-only", action="store_true", help="skip the secondary legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -660,17 +770,17 @@ def main():
     rank, world, local, dist = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    npts = int(np.prod(N_GRID))
-    fac, qc, pc = initial(mg)
+    warmup = max(3, args.warmup)
 
-    g = mg.Propagator(N_GRID, DQ, minv=MINV, device=dev)
-    g.set_potential(mg.MG_POT_ATOM_DIATOM, POT)
-    g.set_separable(fac, qc, pc)
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # the FP64 FMA rate of this GPU: the roofline of the FP64 headline
+    MEASURED["fp64_tflops"] = mg.mg_probe_fma_rate(mg.MG_FP64)
+    MEASURED["fp32_tflops"] = mg.mg_probe_fma_rate(mg.MG_FP32_MIXED)
+
+    g = hh_propagator(mg, HH_N, HH_D, mg.MG_FP64, dev)
+    npts = g.npts
     stream = g.stream
-
-    for _ in range(max(3, args.warmup)):
-        g.propagate(STEPS_PER_CALL, DT, SCHEME)
+    for _ in range(warmup):
+        g.propagate(1, HH_DT, HH_SCHEME)
     g.sync()
 
     def barrier():
@@ -678,18 +788,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # device-resident throughput: events on the library's stream around each call
+    # device-resident throughput: events on the library's stream around each
+    # call; the 6.9 GB state is larger than L2, so nothing is flushed
     launches0 = g.launches
     times = []
     barrier()
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            g.propagate(STEPS_PER_CALL, DT, SCHEME)
+            g.propagate(1, HH_DT, HH_SCHEME)
             e1.record(stream)
             times.append((e0, e1))
         torch.cuda.synchronize(dev)
@@ -698,22 +808,26 @@ def main():
     g.sync()
     launches = g.launches - launches0
     ms = [a.elapsed_time(b) for a, b in times]
-    t_total, units = job_time_and_units(sum(ms) / 1e3, npts * STEPS_PER_CALL * args.steps, dist, device=dev)
+    t_total, units = job_time_and_units(sum(ms) / 1e3, npts * args.steps, dist, device=dev)
     value = units / t_total
 
-    # end to end through the C-ABI with host buffers: upload, propagate, read back
-    psi0 = np.ascontiguousarray(g.get_state()[0])
-    _, q0, p0, _ = g.get_state(want_psi=False)
+    # end to end through the C-ABI with host buffers: every iteration uploads
+    # the state from pinned host memory (mg_upload_u), propagates one step and
+    # reads the state back (mg_download_u)
+    host = torch.empty(npts, dtype=torch.complex128, pin_memory=True)
+    q, p, tt = g.download_u(host)
     barrier()
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(HH_E2E_ITERS):
         t0 = time.perf_counter()
-        g.set_state(psi0, q0, p0, 0.0)
-        g.propagate(STEPS_PER_CALL, DT, SCHEME)
-        out = g.get_state()
+        g.upload_u(host, q, p, tt)
+        g.propagate(1, HH_DT, HH_SCHEME)
+        q, p, tt = g.download_u(host)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = npts * STEPS_PER_CALL * world / statistics.median(e2e_t)
-    del out
+    e2e_value = npts * world / statistics.median(e2e_t)
+    g.close()
+    del g, host
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
@@ -721,52 +835,79 @@ def main():
         return
 
     hbm_peak, hbm_src = peaks()
-    flops_ps = algorithmic_flops_per_point_stage(N_GRID, 2)
-    stages_per_call = STEPS_PER_CALL * STAGES
+    flops_ps = algorithmic_flops_per_point_stage((HH_N,) * HH_D, HH_D)
     t_launch = statistics.mean(ms) / 1e3
-    achieved_tf = flops_ps * npts * stages_per_call / t_launch / 1e12
-    achieved_gbs = algorithmic_bytes_per_point_stage() * npts * stages_per_call / t_launch / 1e9
-    cpu, err = cpu_baseline_and_error(mg, torch)
-    mixed = mixed_precision_leg(mg, torch, dev, args, flush)
-    others = other_workloads(mg, torch, dev, flush)
-    adj = adjoint_leg(mg, torch, dev)
-    batch = batch_leg(mg, torch, dev)
-    orders = order_leg(mg, torch, dev)
-    ensemble = ensemble_leg(mg, torch, dev)
+    ps = npts * HH_STAGES / t_launch
+    achieved_tf = flops_ps * ps / 1e12
+    achieved_gbs = algorithmic_bytes_per_point_stage() * ps / 1e9
+    # the oracle on a bounded sample of the same model: one time step on 12^5,
+    # single-threaded and on every host core; and the GPU's error on it
+    cpu_v, cpu_el = None, None
+    import oracle
+
+    o = hh_oracle(oracle, HH_CPU_D)
+    t0 = time.perf_counter()
+    o.propagate(1, HH_DT, HH_SCHEME)
+    cpu_el = time.perf_counter() - t0
+    cpu_v = HH_N ** HH_CPU_D / cpu_el
+    all_v, ncores, all_slowest, _ = oracle_all_cores(HH_CPU_D)
+    gs = hh_propagator(mg, HH_N, HH_CPU_D, mg.MG_FP64, dev)
+    gs.propagate(1, HH_DT, HH_SCHEME)
+    psi, qs, pss, _ = gs.get_state()
+    psi_o, q_o, p_o, _ = o.get_state()
+    gs.close()
+    err = {"psi_rel_l2": float(np.linalg.norm(psi - psi_o) / np.linalg.norm(psi_o)),
+           "q_abs": float(np.abs(qs - q_o).max()), "p_abs": float(np.abs(pss - p_o).max()),
+           "sample": f"one time step of the same model on a {HH_N}^{HH_CPU_D} grid (same kernel family)"}
+    cpu = {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one time step of the headline model on a {HH_N}^{HH_CPU_D} grid ({cpu_el:.1f} s; the "
+                     f"oracle's cost per point grows with the number of axes, so this favours it), single "
+                     f"thread, {cpu_model()}",
+           "all_cores": {"value": all_v, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": f"the same sample in {ncores} concurrent single-threaded oracle processes "
+                                   f"(slowest {all_slowest:.1f} s)"}}
+
+    secondary = {}
+    if not args.headline_only:
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        secondary["atom_diatom_256"] = atom_diatom_leg(mg, torch, dev, args, flush)
+        secondary["mixed_precision"] = mixed_precision_leg(mg, torch, dev, args, flush)
+        secondary["other_workloads"] = other_workloads(mg, torch, dev, flush)
+        secondary["adjoint"] = adjoint_leg(mg, torch, dev)
+        secondary["batch"] = batch_leg(mg, torch, dev)
+        secondary["error_vs_order"] = order_leg(mg, torch, dev)
+        secondary["ensemble"] = ensemble_leg(mg, torch, dev)
+        del flush
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "warmup": warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(headline_config(world),
-                       l2="flushed (512 MB write) before every timed iteration; the 1 MB state is "
-                          "L2-resident within a call"),
-        "time_steps_per_iteration": STEPS_PER_CALL,
-        "gp_stages_per_s": value * STAGES,
+                       l2="not flushed: the 6.9 GB state is larger than the 129 MB L2"),
+        "gp_stages_per_s": value * HH_STAGES,
         "error_vs_oracle": err,
         "roofline": {
-            "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(),
-            "kernel": "k_propagate (persistent, one launch per call)",
+            "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak(), "unit": "TFLOP/s",
+            "frac": achieved_tf / fp64_peak(), "traffic": traffic_per_launch(),
+            "kernel": "k_propagate_short<double, 12> (persistent, one launch per time step)",
             "flops_per_point_stage": flops_ps,
-            "peak_source": "FP64 FMA units x clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+            "peak_source": "measured in this run: FP64 FMA rate (mg_probe_fma_rate, burst), "
+                           f"nominal {FP64_PEAK_TFLOPS:.3f} = 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "fp32_fma_tflops_measured": MEASURED["fp32_tflops"],
             "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
                     "bytes_per_point_stage": algorithmic_bytes_per_point_stage()},
         },
-        "mixed_precision": mixed,
-        "other_workloads": others,
-        "adjoint": adj,
-        "batch": batch,
-        "error_vs_order": orders,
-        "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
-                "d2h_bytes_per_step": npts * 16 + 2 * 8 * 2,
-                "note": "mg_set_state(host psi) + mg_propagate + mg_get_state(host psi) per iteration"},
+                "d2h_bytes_per_step": npts * 16,
+                "note": "mg_upload_u (pinned host psi) + mg_propagate + mg_download_u (pinned host psi) per "
+                        f"iteration, median of {HH_E2E_ITERS}"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    line.update(secondary)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -87,6 +87,24 @@ size_t mg_workspace_bytes(int D, const int64_t* N, int precision);
 mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv,
                     double hbar, int precision, void* d_psi, void* d_work, size_t work_bytes,
                     void* cuda_stream);
+
+/* mg_create with a choice of kernel (flags = 0 is mg_create).  The method is
+ * the same whichever kernel runs; the flags select how the transforms move
+ * through memory and which units compute them.
+ *  MG_CREATE_GENERAL_KERNEL  never use the short-axis kernel (one pass per axis)
+ *  MG_CREATE_NO_TMA          short-axis kernel with cp.async chunk copies only
+ *  MG_CREATE_TC_TF32X3       short-axis kernel (TMA copies) whose 16-point line
+ *                            DFTs run on the tensor cores as a GEMM with
+ *                            3xTF32 split products accumulated in FP32
+ *  MG_CREATE_TC_BF16X3       the same with BF16x3 split products (each value
+ *                            split into three bfloat16 terms, six products)
+ * The two tensor-core flags need an MG_FP32_MIXED grid of D >= 3 axes of 16
+ * points each (MG_ERR_UNSUPPORTED otherwise); at most one of them, and
+ * neither with the first two flags (MG_ERR_ARG). */
+enum { MG_CREATE_GENERAL_KERNEL = 1, MG_CREATE_NO_TMA = 2, MG_CREATE_TC_TF32X3 = 4, MG_CREATE_TC_BF16X3 = 8 };
+mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv,
+                       double hbar, int precision, void* d_psi, void* d_work, size_t work_bytes,
+                       void* cuda_stream, int flags);
 mg_status mg_destroy(mg_ctx* ctx);
 
 /* Select the potential (eq:hamiltonian); layouts above. */
@@ -96,6 +114,19 @@ mg_status mg_set_potential(mg_ctx* ctx, int kind, const double* params, int npar
  * prod(N) complex values) sampled on the grid centred at (q, p), with time t.
  * psi == NULL keeps the device state and only sets (q, p, t). */
 mg_status mg_set_state(mg_ctx* ctx, const double* psi, const double* q, const double* p, double t);
+
+/* Host-buffer state transfer without conversion, for callers that keep the
+ * state in host memory between calls (the scaled state u^J = psi(x^J)
+ * sqrt(prod dq_l) in the storage precision: prod(N) interleaved complex128
+ * values for MG_FP64, complex64 for MG_FP32_MIXED).
+ * mg_upload_u: copy host_u into d_psi on the context's stream and set the
+ *   grid centres (q, p) and time t; asynchronous: host_u must stay valid and
+ *   unchanged until the stream has reached the copy.  Page-locked host_u
+ *   (cudaHostAlloc, or a pinned torch tensor) copies at full link bandwidth.
+ * mg_download_u: copy d_psi into host_u and return q, p, t (each may be
+ *   NULL); synchronises the stream and reports any pending device status. */
+mg_status mg_upload_u(mg_ctx* ctx, const void* host_u, const double* q, const double* p, double t);
+mg_status mg_download_u(mg_ctx* ctx, void* host_u, double* q, double* p, double* t);
 
 /* Build a separable initial state on the grid centred at (q_ctr, p_ctr), t=0.
  * Per axis l, kinds[l] and params[4*l .. 4*l+3]:
@@ -147,6 +178,17 @@ mg_status mg_inner_product(mg_ctx* a, const mg_ctx* b, double* re, double* im);
 /* Synchronise the context's stream and report any pending device status. */
 mg_status mg_sync(mg_ctx* ctx);
 
+/* Failure-detection test hook; the paper has no counterpart.  Arms the next
+ * mg_propagate of this context so that its first grid-wide barrier cannot
+ * complete (the barrier word starts with every CTA already counted in the
+ * current generation, so no arrival is the last one) and each barrier wait
+ * gives up after limit_s seconds (0 < limit_s <= 5) instead of 5 s.  Every
+ * CTA then records MG_ERR_TIMEOUT and returns: the next synchronising call
+ * reports it, the state is left partly propagated, and later calls run
+ * normally (every launch starts from a cleared barrier word).  Nothing waits
+ * without a limit.  MG_ERR_ARG for a NULL context or limit_s out of range. */
+mg_status mg_test_stuck_barrier(mg_ctx* ctx, double limit_s);
+
 /* Reverse-mode derivative of the last mg_propagate call, by the reversible
  * adjoint: the context's state must be the final state of that call (same
  * n_steps, dt, scheme, split, grid_motion).  Each substep of Sec. II.G is undone
@@ -175,10 +217,10 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
  * several axes transformed per pass over the state), 2 = the same kernel
  * moving its chunks with TMA tensor copies (FP32 storage, 16-point axes),
  * 0 = the general kernel (one pass per axis), -1 for a NULL context or no
- * potential yet.  The same
- * method either way (Sec. II.G); only the memory traffic differs.  Setting
- * the environment variable MG_SHORT_AXES=0 before mg_create turns the
- * short-axis kernel off for that context. */
+ * potential yet; 3 and 4 = the short-axis kernel with TMA copies and its
+ * line DFTs on the tensor cores (3xTF32 and BF16x3 split products,
+ * mg_create_ex).  The same method either way (Sec. II.G); only the memory
+ * traffic and the arithmetic units differ.  mg_create_ex's flags choose. */
 int mg_propagate_path(const mg_ctx* ctx);
 
 /* Host-only (no GPU): the stage coefficients gamma_1..gamma_S of a named
@@ -202,6 +244,21 @@ int mg_scheme_coefficients(const char* scheme, double* gamma, int max);
 int mg_short_axis_plan(int D, const int64_t* N, int precision, int* first_axis, int* naxes, int* threads,
                        int* smem_bytes);
 
+/* ---- Diagnostics of the device arithmetic (no counterpart in the paper) ----
+ * mg_probe_fma_rate: the measured fused multiply-add rate of the current GPU
+ * in TFLOP/s (2 flop per FMA), FP64 (precision = MG_FP64) or FP32
+ * (MG_FP32_MIXED): independent FMA chains on every SM, best of three timed
+ * launches after a warm-up, on cuda_stream (synchronised).  The FP64
+ * propagation is bound by the FP64 units, and its roofline is stated against
+ * this rate.
+ * mg_probe_expi: e^{i theta} as the kernels evaluate it for their phase
+ * factors (table-driven sine and cosine after Tang, with a three-word
+ * Cody-Waite reduction by pi/128), for n arguments d_theta (device FP64),
+ * written to d_sin and d_cos (device FP64, n each); synchronises cuda_stream.
+ * Neither allocates device memory. */
+mg_status mg_probe_fma_rate(int precision, void* cuda_stream, double* tflops);
+mg_status mg_probe_expi(const double* d_theta, double* d_sin, double* d_cos, int64_t n, void* cuda_stream);
+
 /* <x> under the Morse ground state above (host quadrature helper for
  * choosing an initial grid centre). */
 double mg_morse_mean(double Dm, double a, double re, double mass, double hbar);
@@ -222,12 +279,17 @@ const char* mg_status_string(int status);
  *  - d_psi: device buffer of prod(N) complex128 values holding the scaled
  *    state u^J = psi(x^J) sqrt(prod dq_l), updated in place.  FP64 only.
  *  - q, p: host arrays of D doubles, the grid centres on entry and on exit.
+ *  - grid_motion: MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P or
+ *    MG_GRID_FIXED; MG_GRID_NAIVE returns MG_ERR_UNSUPPORTED (it needs the
+ *    context's state-sized scratch buffer).
  *  - Other arguments as in mg_create, mg_set_potential and mg_propagate.
  *  - Limits: sum of the axis lengths <= 4096 and at most 1024 CTAs; larger
  *    grids return MG_ERR_UNSUPPORTED before any device work.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The array's device address is looked up (cudaGetSymbolAddress, with
+ *    the device current) by the first call on each device and kept for the
+ *    process; that first call should come before any stream capture begins
+ *    on the device.  The kept address does not survive cudaDeviceReset: do
+ *    not call this entry point again in a process after a device reset.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other host threads) race and corrupt each other.  The call
  *    synchronises `cuda_stream` before it returns. */

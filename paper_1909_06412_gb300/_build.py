@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libmgrid.so")
-SOURCES = ["mg_kernels.cu", "mg_short.cu", "mg_regrid.cu", "mg_adjoint.cu", "mg_batch.cu", "mg_capi.cu"]
+SOURCES = ["mg_kernels.cu", "mg_short.cu", "mg_regrid.cu", "mg_adjoint.cu", "mg_batch.cu", "mg_capi.cu",
+           "mg_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I" + os.path.join(ROOT, "include"), "-I" + SRC]

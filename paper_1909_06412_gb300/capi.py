@@ -21,11 +21,13 @@ MG_FP64, MG_FP32_MIXED = 0, 1
 MG_TVT, MG_VTV, MG_TV = 0, 1, 2
 MG_GRID_ADAPTIVE, MG_GRID_ADAPTIVE_CENTRE_P, MG_GRID_FIXED, MG_GRID_NAIVE = 0, 1, 2, 3
 MG_POT_HARMONIC, MG_POT_ATOM_DIATOM, MG_POT_HENON_HEILES, MG_POT_SECREST_JOHNSON = 0, 1, 2, 3
+MG_CREATE_GENERAL_KERNEL, MG_CREATE_NO_TMA, MG_CREATE_TC_TF32X3, MG_CREATE_TC_BF16X3 = 1, 2, 4, 8
 
 __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "MgError", "lib", "mg_workspace_bytes",
                                                         "mg_batch_workspace_bytes", "mg_morse_mean",
                                                         "mg_propagate_noalloc", "mg_short_axis_plan",
-                                                        "mg_scheme_coefficients"]
+                                                        "mg_scheme_coefficients", "mg_probe_fma_rate",
+                                                        "mg_probe_expi"]
 
 _lib = None
 
@@ -41,6 +43,7 @@ def lib():
         L.mg_workspace_bytes.argtypes = [i32, vp, i32]
         L.mg_workspace_bytes.restype = sz
         L.mg_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, d, i32, vp, vp, sz, vp]
+        L.mg_create_ex.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, d, i32, vp, vp, sz, vp, i32]
         L.mg_destroy.argtypes = [vp]
         L.mg_set_potential.argtypes = [vp, i32, vp, i32]
         L.mg_set_state.argtypes = [vp, vp, vp, vp, d]
@@ -49,6 +52,11 @@ def lib():
         L.mg_get_state.argtypes = [vp, vp, vp, vp, vp]
         L.mg_get_observables.argtypes = [vp, vp, vp, vp, vp]
         L.mg_sync.argtypes = [vp]
+        L.mg_test_stuck_barrier.argtypes = [vp, d]
+        L.mg_upload_u.argtypes = [vp, vp, vp, vp, d]
+        L.mg_download_u.argtypes = [vp, vp, vp, vp, vp]
+        L.mg_probe_fma_rate.argtypes = [i32, vp, vp]
+        L.mg_probe_expi.argtypes = [vp, vp, vp, i64, vp]
         L.mg_regrid.argtypes = [vp, vp, vp]
         L.mg_inner_product.argtypes = [vp, vp, vp, vp]
         L.mg_kernel_launches.argtypes = [vp]
@@ -71,10 +79,11 @@ def lib():
         L.mg_batch_sync.argtypes = [vp, vp]
         L.mg_batch_info.argtypes = [vp, vp, vp, vp, vp]
         L.mg_batch_destroy.argtypes = [vp]
-        for name in ("mg_create", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
-                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_adjoint", "mg_regrid", "mg_inner_product",
+        for name in ("mg_create", "mg_create_ex", "mg_destroy", "mg_set_potential", "mg_set_state", "mg_set_separable",
+                     "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_test_stuck_barrier",
+                     "mg_adjoint", "mg_regrid", "mg_inner_product",
                      "mg_batch_create", "mg_batch_propagate", "mg_batch_sync", "mg_batch_info",
-                     "mg_batch_destroy"):
+                     "mg_batch_destroy", "mg_probe_fma_rate", "mg_probe_expi", "mg_upload_u", "mg_download_u"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -137,10 +146,32 @@ def mg_morse_mean(Dm, a, re, mass, hbar=1.0):
     return float(lib().mg_morse_mean(Dm, a, re, mass, hbar))
 
 
+def mg_probe_fma_rate(precision=MG_FP64, stream=None):
+    """Measured FMA rate of the current GPU in TFLOP/s (FP64 or FP32)."""
+    out = np.zeros(1)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(lib().mg_probe_fma_rate(precision, s, _ptr(out)), "mg_probe_fma_rate")
+    return float(out[0])
+
+
+def mg_probe_expi(theta, stream=None):
+    """The kernels' table-driven (sin, cos) at the CUDA float64 tensor theta."""
+    import torch
+
+    th = theta.contiguous()
+    if th.dtype != torch.float64 or not th.is_cuda:
+        raise ValueError("theta must be a CUDA float64 tensor")
+    s, c = torch.empty_like(th), torch.empty_like(th)
+    st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(lib().mg_probe_expi(ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                               ctypes.c_void_p(c.data_ptr()), th.numel(), st), "mg_probe_expi")
+    return s, c
+
+
 class Propagator:
     """One grid context whose state and workspace live in torch CUDA tensors."""
 
-    def __init__(self, N, dq, minv=None, hbar=1.0, precision=MG_FP64, device=None, stream=None):
+    def __init__(self, N, dq, minv=None, hbar=1.0, precision=MG_FP64, device=None, stream=None, flags=0):
         import torch
 
         self.torch = torch
@@ -164,10 +195,11 @@ class Propagator:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         n = np.ascontiguousarray(self.N, dtype=np.int64)
         h = ctypes.c_void_p()
-        rc = lib().mg_create(ctypes.byref(h), self.D, _ptr(n), _ptr(self.dq), _ptr(self.minv), self.hbar,
-                             precision, ctypes.c_void_p(self.psi.data_ptr()), ctypes.c_void_p(self.work.data_ptr()),
-                             ws, ctypes.c_void_p(self.stream.cuda_stream))
-        _check(rc, "mg_create")
+        rc = lib().mg_create_ex(ctypes.byref(h), self.D, _ptr(n), _ptr(self.dq), _ptr(self.minv), self.hbar,
+                                precision, ctypes.c_void_p(self.psi.data_ptr()),
+                                ctypes.c_void_p(self.work.data_ptr()), ws, ctypes.c_void_p(self.stream.cuda_stream),
+                                int(flags))
+        _check(rc, "mg_create_ex")
         self._h = h
 
     def close(self):
@@ -200,6 +232,28 @@ class Propagator:
             ptr = _ptr(arr)
         _check(lib().mg_set_state(self._h, ptr, _ptr(q), _ptr(p), float(t)), "mg_set_state")
 
+    def upload_u(self, host_u, q, p, t=0.0):
+        """mg_upload_u: host_u is a CPU tensor (ideally pinned) of the storage
+        dtype (complex128 / complex64) holding the scaled state u."""
+        q, p = _f64(q, self.D), _f64(p, self.D)
+        self._check_host(host_u)
+        _check(lib().mg_upload_u(self._h, ctypes.c_void_p(host_u.data_ptr()), _ptr(q), _ptr(p), float(t)),
+               "mg_upload_u")
+
+    def download_u(self, host_u):
+        """mg_download_u into a CPU tensor like upload_u's; returns (q, p, t)."""
+        self._check_host(host_u)
+        q, p, t = np.empty(self.D), np.empty(self.D), np.zeros(1)
+        _check(lib().mg_download_u(self._h, ctypes.c_void_p(host_u.data_ptr()), _ptr(q), _ptr(p), _ptr(t)),
+               "mg_download_u")
+        return q, p, float(t[0])
+
+    def _check_host(self, a):
+        torch = self.torch
+        want = torch.complex128 if self.precision == MG_FP64 else torch.complex64
+        if a.is_cuda or a.dtype != want or a.numel() != self.npts or not a.is_contiguous():
+            raise ValueError(f"host buffer must be a contiguous CPU {want} tensor of {self.npts} values")
+
     def set_separable(self, factors, q_ctr, p_ctr):
         """factors: per axis ('gauss', q0, p0, sigma) or ('morse', Dm, a, re, mass)."""
         kinds = np.zeros(self.D, dtype=np.int32)
@@ -216,6 +270,12 @@ class Propagator:
 
     def sync(self):
         _check(lib().mg_sync(self._h), "mg_sync")
+
+    def test_stuck_barrier(self, limit_s):
+        """Failure-detection test hook (mg_test_stuck_barrier): the next
+        propagate() cannot pass its first grid barrier and gives up after
+        limit_s seconds with MG_ERR_TIMEOUT."""
+        _check(lib().mg_test_stuck_barrier(self._h, float(limit_s)), "mg_test_stuck_barrier")
 
     def inner_product(self, other):
         """<psi_self | psi_other>, other's state interpolated onto this grid."""
@@ -268,7 +328,8 @@ class Propagator:
 
     @property
     def path(self):
-        """Kernel of mg_propagate: 0 general, 1 short-axis, 2 short-axis with TMA copies."""
+        """Kernel of mg_propagate: 0 general, 1 short-axis, 2 short-axis with TMA
+        copies, 3 / 4 the same with tensor-core line DFTs (3xTF32 / BF16x3)."""
         return int(lib().mg_propagate_path(self._h))
 
 

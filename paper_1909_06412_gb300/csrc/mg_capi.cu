@@ -23,11 +23,12 @@ void* init_tables_kernel(int prec);
 void* obs_tables_kernel(int prec);
 void* set_product_kernel(int prec);
 void* adjoint_kernel(int kind);
-void* short_kernel(int prec, int n, int tma);
+void* short_kernel(int prec, int n, int tma, int tc);
 void* regrid_kernel(int prec, int kind);
 void* inner_kernel(int prec);
 int short_threads_for(int prec, int n);
-int short_lpc_for(int prec, int n);
+int short_lpc_for(int prec, int n, int tc);
+int short_tc_smem_bytes(int tc);
 }  // namespace mgk
 
 using namespace mgk;
@@ -215,6 +216,7 @@ void tile_plan(Plan& P) {
 // carve_short() in mg_short.cu.
 bool short_smem(const Plan& P, ShortPlan& SP, int re) {
   auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t tcb = (size_t)short_tc_smem_bytes(SP.tc);
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
   const size_t TT = (size_t)P.tab_total, n = (size_t)SP.n;
@@ -224,7 +226,7 @@ bool short_smem(const Plan& P, ShortPlan& SP, int re) {
   const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
   for (int nreg = 3; nreg >= 2; --nreg) {
     // + up to 1008 bytes per region to start it on a 1024-byte boundary
-    const size_t total = tabs + (size_t)nreg * (r16(vs * (size_t)re) + 1008);
+    const size_t total = tabs + (size_t)nreg * (r16(vs * (size_t)re) + 1008) + tcb;
     if (total <= cap) {
       SP.region_elems = re;
       SP.nreg = nreg;
@@ -241,14 +243,15 @@ bool short_smem(const Plan& P, ShortPlan& SP, int re) {
 // most axes whose blocks tile a chunk; the other groups, from the back, the
 // most axes (up to SHORT_MAXG) whose chunk rows of WT adjacent elements are
 // at least 32 bytes (one DRAM sector) and divide the trailing index range.
-bool short_plan(const Plan& P, ShortPlan& SP) {
+bool short_plan(const Plan& P, ShortPlan& SP, int tc = 0) {
   std::memset(&SP, 0, sizeof(ShortPlan));
+  SP.tc = tc;
   const int D = P.D;
   const int n = short_shape(D, P.N);
   if (!n) return false;
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const int threads = short_threads_for(P.prec, n);
-  const int lpc = short_lpc_for(P.prec, n);
+  const int lpc = short_lpc_for(P.prec, n, tc);
   auto pw = [&](int k) {
     int64_t r = 1;
     for (int i = 0; i < k; ++i) r *= n;
@@ -397,32 +400,46 @@ bool short_tma_smem(const Plan& P, ShortPlan& SP) {
 // ---- composition coefficients (eq:comp_TVT; Yoshida 1990 triple jump,
 // ---- Suzuki 1990 fractal), built by recursion on the order -----------------
 
-bool scheme_coeffs(const char* name, std::vector<double>& g) {
-  if (!name) return false;
-  std::string s(name);
+// Stage coefficients of a named scheme into g[0 .. cap-1]; returns the number
+// of stages S, or -1 for an unknown name or S > cap.  No heap use: the
+// allocation-free entry point shares this generator.
+int scheme_fill(const char* name, double* g, int cap) {
+  if (!name || cap < 1) return -1;
   int family = -1, order = 0;
-  if (s == "strang") { family = 0; order = 2; }
-  else if (s.rfind("yoshida", 0) == 0) { family = 1; order = std::atoi(s.c_str() + 7); }
-  else if (s.rfind("suzuki", 0) == 0) { family = 2; order = std::atoi(s.c_str() + 6); }
-  if (family < 0 || order < 2 || order > 10 || order % 2) return false;
-  g.assign(1, 1.0);
+  if (std::strcmp(name, "strang") == 0) { family = 0; order = 2; }
+  else if (std::strncmp(name, "yoshida", 7) == 0) { family = 1; order = std::atoi(name + 7); }
+  else if (std::strncmp(name, "suzuki", 6) == 0) { family = 2; order = std::atoi(name + 6); }
+  if (family < 0 || order < 2 || order > 10 || order % 2) return -1;
+  double tmp[MAX_STAGES];
+  int s = 1;
+  g[0] = 1.0;
   for (int k = 1; 2 * k < order; ++k) {
     // raise the order from 2k to 2k+2
     const double e = 1.0 / (2 * k + 1);
-    std::vector<double> w;
+    double w[5];
+    int nw;
     if (family == 1) {
       const double a = 1.0 / (2.0 - std::pow(2.0, e));
-      w = {a, 1.0 - 2.0 * a, a};
+      w[0] = a; w[1] = 1.0 - 2.0 * a; w[2] = a; nw = 3;
     } else {
       const double a = 1.0 / (4.0 - std::pow(4.0, e));
-      w = {a, a, 1.0 - 4.0 * a, a, a};
+      w[0] = a; w[1] = a; w[2] = 1.0 - 4.0 * a; w[3] = a; w[4] = a; nw = 5;
     }
-    std::vector<double> next;
-    for (double wi : w)
-      for (double gi : g) next.push_back(wi * gi);
-    g.swap(next);
+    if (s * nw > cap || s * nw > MAX_STAGES) return -1;
+    for (int b = 0; b < nw; ++b)
+      for (int i = 0; i < s; ++i) tmp[b * s + i] = w[b] * g[i];
+    s *= nw;
+    std::memcpy(g, tmp, sizeof(double) * s);
   }
-  return (int)g.size() <= MAX_STAGES;
+  return s;
+}
+
+bool scheme_coeffs(const char* name, std::vector<double>& g) {
+  g.assign(MAX_STAGES, 0.0);
+  const int s = scheme_fill(name, g.data(), MAX_STAGES);
+  if (s < 1) return false;
+  g.resize(s);
+  return true;
 }
 
 // Host twin of the kernels' round_unit_f32: the float pair bracketing (x, y)
@@ -481,6 +498,7 @@ struct mg_ctx {
   double q[MAXD], p[MAXD], t;
   bool pot_set, state_set;
   bool tables_stale;  // the grid centre moved in a batched launch; A tables to rebuild
+  double stuck_barrier_s;  // test hook: > 0 arms a barrier that cannot complete (mg_test_stuck_barrier)
   int64_t launches;
   std::vector<double> host;  // staging for psi
   std::vector<double> gam;
@@ -570,7 +588,17 @@ size_t mg_workspace_bytes(int D, const int64_t* N, int precision) {
 
 mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv, double hbar,
                     int precision, void* d_psi, void* d_work, size_t work_bytes, void* cuda_stream) {
+  return mg_create_ex(out, D, N, dq, minv, hbar, precision, d_psi, d_work, work_bytes, cuda_stream, 0);
+}
+
+mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv, double hbar,
+                       int precision, void* d_psi, void* d_work, size_t work_bytes, void* cuda_stream, int flags) {
   if (!out || !N || !dq || !minv || !d_psi || !d_work) return MG_ERR_ARG;
+  if (flags & ~(MG_CREATE_GENERAL_KERNEL | MG_CREATE_NO_TMA | MG_CREATE_TC_TF32X3 | MG_CREATE_TC_BF16X3))
+    return MG_ERR_ARG;
+  if ((flags & MG_CREATE_TC_TF32X3) && (flags & MG_CREATE_TC_BF16X3)) return MG_ERR_ARG;
+  const int want_tc = (flags & MG_CREATE_TC_TF32X3) ? 1 : ((flags & MG_CREATE_TC_BF16X3) ? 2 : 0);
+  if (want_tc && (flags & (MG_CREATE_GENERAL_KERNEL | MG_CREATE_NO_TMA))) return MG_ERR_ARG;
   *out = nullptr;
   if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar)) return MG_ERR_ARG;
   if (precision != MG_FP64 && precision != MG_FP32_MIXED) return MG_ERR_ARG;
@@ -664,15 +692,15 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
   B.scratch = (double2*)(w + L.scratch);
 
   // short-axis kernel: one CTA per SM, all co-resident
-  const char* se = std::getenv("MG_SHORT_AXES");
-  if ((!se || std::atoi(se) != 0) && short_plan(P, c->SP)) {
-    c->SP.tma = short_tma_maps(P, c->SP, d_psi) ? 1 : 0;
+  if (!(flags & MG_CREATE_GENERAL_KERNEL) && short_plan(P, c->SP, want_tc)) {
+    c->SP.tma = !(flags & MG_CREATE_NO_TMA) && short_tma_maps(P, c->SP, d_psi) ? 1 : 0;
     if (c->SP.tma && !short_tma_smem(P, c->SP)) c->SP.tma = 0;
-    void* fn = short_kernel(P.prec, c->SP.n, c->SP.tma);
+    void* fn = short_kernel(P.prec, c->SP.n, c->SP.tma, c->SP.tc);
     int occ = 0;
+    // the tensor-core variant holds 64 TMEM columns per CTA (512 per SM)
     if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->SP.smem_bytes) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->SP.threads, c->SP.smem_bytes) == cudaSuccess &&
-        occ >= 1) {
+        occ >= 1 && (!c->SP.tc || occ * 64 <= 512)) {
       c->SP.nblocks = std::min(MAXBLOCKS, occ * sms);
       c->SP.tabF = (double2*)(w + L.tabF);
       c->SP.tabP = (double2*)(w + L.tabP);
@@ -683,6 +711,12 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
       cudaGetLastError();
       c->SP.on = 0;
     }
+  }
+  if (want_tc && !(c->SP.on && c->SP.tma && c->SP.tc)) {
+    // the tensor-core line DFTs exist for FP32 grids of 16-point axes whose
+    // chunks move by TMA copies only
+    delete c;
+    return MG_ERR_UNSUPPORTED;
   }
 
   // static tables: twiddles e^{-2 pi i m/N_l} and k - N_l/2
@@ -778,6 +812,33 @@ mg_status mg_set_state(mg_ctx* c, const double* psi, const double* q, const doub
   if (s == MG_OK) s = init_tables(c);
   if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
   if (s == MG_OK) c->state_set = true;
+  return s;
+}
+
+mg_status mg_upload_u(mg_ctx* c, const void* host_u, const double* q, const double* p, double t) {
+  if (!c || !host_u || !q || !p || !std::isfinite(t)) return MG_ERR_ARG;
+  for (int a = 0; a < c->P.D; ++a)
+    if (!std::isfinite(q[a]) || !std::isfinite(p[a])) return MG_ERR_ARG;
+  const size_t bytes = (size_t)c->P.npts * (c->P.prec == 0 ? sizeof(double2) : sizeof(float2));
+  mg_status s = cuda_ok(cudaMemcpyAsync(c->B.psi, host_u, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (s != MG_OK) return s;
+  for (int a = 0; a < c->P.D; ++a) {
+    c->q[a] = q[a];
+    c->p[a] = p[a];
+  }
+  c->t = t;
+  s = upload_ctrl(c);
+  if (s == MG_OK) s = init_tables(c);
+  if (s == MG_OK) c->state_set = true;
+  return s;
+}
+
+mg_status mg_download_u(mg_ctx* c, void* host_u, double* q, double* p, double* t) {
+  if (!c || !host_u) return MG_ERR_ARG;
+  if (!c->state_set) return MG_ERR_STATE;
+  const size_t bytes = (size_t)c->P.npts * (c->P.prec == 0 ? sizeof(double2) : sizeof(float2));
+  mg_status s = cuda_ok(cudaMemcpyAsync(host_u, c->B.psi, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (s == MG_OK) s = mg_get_state(c, nullptr, q, p, t);  // synchronises, reports the status
   return s;
 }
 
@@ -890,11 +951,24 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
                                         cudaMemcpyHostToDevice, c->stream));
   if (s == MG_OK) s = cuda_ok(cudaMemsetAsync(c->B.bar, 0, 64 * sizeof(unsigned), c->stream));
   if (s != MG_OK) return s;
-  if (c->SP.on && uses_short_kernel(c->P)) {
+  const bool short_path = c->SP.on && uses_short_kernel(c->P);
+  Bufs B = c->B;
+  if (c->stuck_barrier_s > 0) {
+    // test hook: the barrier word starts with gridDim.x arrivals of the
+    // current generation, so no arrival is ever the last one; every CTA's
+    // wait runs out after the short limit and the kernel returns
+    const unsigned long long word = (unsigned long long)(short_path ? c->SP.nblocks : c->P.nblocks);
+    s = cuda_ok(cudaMemcpyAsync(c->B.bar, &word, sizeof(word), cudaMemcpyHostToDevice, c->stream));
+    if (s == MG_OK) s = cuda_ok(cudaStreamSynchronize(c->stream));
+    if (s != MG_OK) return s;
+    B.bar_limit_ns = (uint64_t)(c->stuck_barrier_s * 1e9);
+    c->stuck_barrier_s = 0;
+  }
+  if (short_path) {
     ShortPlan SP = c->SP;
     SP.pairs = c->P.pot_kind == MG_POT_HENON_HEILES;
-    void* sfn = short_kernel(c->P.prec, SP.n, SP.tma);
-    void* sargs[] = {&c->P, &c->B, &R, &SP};
+    void* sfn = short_kernel(c->P.prec, SP.n, SP.tma, SP.tc);
+    void* sargs[] = {&c->P, &B, &R, &SP};
     cudaError_t e = cudaLaunchCooperativeKernel(sfn, dim3(SP.nblocks), dim3(SP.threads), sargs, SP.smem_bytes,
                                                 c->stream);
     c->launches++;
@@ -907,11 +981,17 @@ mg_status mg_propagate(mg_ctx* c, int64_t n_steps, double dt, const char* scheme
   if (c->P.smem_bytes > 48 * 1024 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->P.smem_bytes) != cudaSuccess)
     return MG_ERR_CUDA;
-  void* args[] = {&c->P, &c->B, &R};
+  void* args[] = {&c->P, &B, &R};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->P.nblocks), dim3(THREADS), args, c->P.smem_bytes, c->stream);
   c->launches++;
   if (e != cudaSuccess) return MG_ERR_CUDA;
   c->t += (double)n_steps * dt;
+  return MG_OK;
+}
+
+mg_status mg_test_stuck_barrier(mg_ctx* c, double limit_s) {
+  if (!c || !(limit_s > 0) || !(limit_s <= 5.0)) return MG_ERR_ARG;
+  c->stuck_barrier_s = limit_s;
   return MG_OK;
 }
 
@@ -1166,6 +1246,7 @@ int64_t mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : -1; }
 int mg_propagate_path(const mg_ctx* c) {
   if (!c || !c->pot_set) return -1;
   if (!c->SP.on || !uses_short_kernel(c->P)) return 0;
+  if (c->SP.tc) return 2 + c->SP.tc;
   return c->SP.tma ? 2 : 1;
 }
 
@@ -1291,37 +1372,6 @@ mg_status noalloc_scratch(void** out) {
   return MG_OK;
 }
 
-// Composition coefficients into a fixed array (no heap use).
-int scheme_fixed(const char* name, double* g, int cap) {
-  if (!name) return -1;
-  int family = -1, order = 0;
-  if (std::strcmp(name, "strang") == 0) { family = 0; order = 2; }
-  else if (std::strncmp(name, "yoshida", 7) == 0) { family = 1; order = std::atoi(name + 7); }
-  else if (std::strncmp(name, "suzuki", 6) == 0) { family = 2; order = std::atoi(name + 6); }
-  if (family < 0 || order < 2 || order > 10 || order % 2) return -1;
-  double tmp[MAX_STAGES];
-  int s = 1;
-  g[0] = 1.0;
-  for (int k = 1; 2 * k < order; ++k) {
-    const double e = 1.0 / (2 * k + 1);
-    double w[5];
-    int nw;
-    if (family == 1) {
-      const double a = 1.0 / (2.0 - std::pow(2.0, e));
-      w[0] = a; w[1] = 1.0 - 2.0 * a; w[2] = a; nw = 3;
-    } else {
-      const double a = 1.0 / (4.0 - std::pow(4.0, e));
-      w[0] = a; w[1] = a; w[2] = 1.0 - 4.0 * a; w[3] = a; w[4] = a; nw = 5;
-    }
-    if (s * nw > cap) return -1;
-    for (int b = 0; b < nw; ++b)
-      for (int i = 0; i < s; ++i) tmp[b * s + i] = w[b] * g[i];
-    s *= nw;
-    std::memcpy(g, tmp, sizeof(double) * s);
-  }
-  return s;
-}
-
 }  // namespace
 
 extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double* dq, const double* minv,
@@ -1333,6 +1383,9 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar) || n_steps < 0 || !std::isfinite(dt))
     return MG_ERR_ARG;
   if (split != MG_TVT && split != MG_VTV && split != MG_TV) return MG_ERR_ARG;
+  // the naive grid (one host round trip and regrid per step) needs the
+  // context's scratch state buffer: not offered here
+  if (grid_motion == MG_GRID_NAIVE) return MG_ERR_UNSUPPORTED;
   if (grid_motion != MG_GRID_ADAPTIVE && grid_motion != MG_GRID_ADAPTIVE_CENTRE_P && grid_motion != MG_GRID_FIXED)
     return MG_ERR_ARG;
   if ((uintptr_t)d_psi & 15) return MG_ERR_ARG;
@@ -1363,7 +1416,7 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   for (int i = 0; i < npot; ++i)
     if (!std::isfinite(pot_params[i])) return MG_ERR_ARG;
   double gam[MAX_STAGES];
-  const int S = scheme_fixed(scheme, gam, MAX_STAGES);
+  const int S = scheme_fill(scheme, gam, MAX_STAGES);
   if (S <= 0) return MG_ERR_ARG;
   if (n_steps == 0) return MG_OK;
 

@@ -278,7 +278,8 @@ constexpr uint64_t BARRIER_LIMIT_NS = 5000000000ull;  // 5 s
 constexpr unsigned BARRIER_MAX_SPINS = 400000000u;
 
 // All CTAs of the (cooperative) grid must call this.  Returns false after a
-// timeout; the status word then holds ST_TIMEOUT.
+// timeout (B.bar_limit_ns, else BARRIER_LIMIT_NS, or BARRIER_MAX_SPINS
+// spins); the status word then holds ST_TIMEOUT.
 //
 // One 64-bit word holds the generation (high half) and the arrivals of the
 // current generation (low half).  An arriving CTA adds 1 and learns the
@@ -299,11 +300,12 @@ __device__ bool grid_sync(const Bufs& B, int* sflag) {
       atomicAdd(word, (1ull << 32) - gridDim.x);
     } else {
       const uint64_t t0 = global_ns();
+      const uint64_t limit = B.bar_limit_ns ? B.bar_limit_ns : BARRIER_LIMIT_NS;
       unsigned spins = 0;
       while ((unsigned)(ld_acquire_u64(word) >> 32) == g0) {
         if (spins > 64) __nanosleep(20);
         ++spins;
-        if ((spins & 127u) == 0 && (global_ns() - t0 > BARRIER_LIMIT_NS || spins > BARRIER_MAX_SPINS)) {
+        if ((spins & 127u) == 0 && (global_ns() - t0 > limit || spins > BARRIER_MAX_SPINS)) {
           ok = 0;
           atomicExch(B.status, ST_TIMEOUT);
           break;

@@ -71,6 +71,7 @@ struct Bufs {
   const double* gamma;   // composition coefficients
   double2* sct;          // 256 entries e^{i k pi / 128}
   double2* scratch;      // npts complex128 (observables, host staging)
+  uint64_t bar_limit_ns; // time limit of a grid-barrier wait (0 = the default 5 s)
 };
 
 // One persistent launch.

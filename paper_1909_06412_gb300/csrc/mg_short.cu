@@ -42,6 +42,7 @@
 
 #include "mg_device.cuh"
 #include "mg_short.h"
+#include "mg_tc.cuh"
 
 namespace mgk {
 namespace {
@@ -55,6 +56,10 @@ namespace {
 // beat 9 by 3.5% and 8 by 7%).  Sixteen warps with 128 registers each spill
 // in the fused passes.
 constexpr int short_lpc(int prec, int n) { return n % 3 == 0 ? (prec ? 576 : 288) : (prec ? 512 : 256); }
+// The tensor-core variant (FP32, 16-point lines) holds 256 lines per chunk,
+// one per thread: one round of 128-line GEMMs per warpgroup and axis, and
+// room in shared memory for the operands beside three chunk regions.
+constexpr int short_lpc_tc(int prec, int n, int tc) { return tc ? 256 : short_lpc(prec, n); }
 constexpr int short_threads(int prec, int n) { return n % 3 == 0 ? (prec ? 288 : 384) : 256; }
 
 enum { SM_NONE = 0, SM_KIN = 1, SM_V = 2, SM_VONLY = 3 };
@@ -216,6 +221,12 @@ template <typename V, typename T> struct SSm {
   V* Pt;      // [(D-1)*n*n] pair factors
   T* col;     // [5][D*n] f', g, g', h, h'
   V* reg[3];
+  // tensor-core DFT (ShortPlan::tc != 0): B operands of the group's axes,
+  // A operands of the two warpgroups, their MMA barriers, the TMEM address
+  unsigned char* tcb;
+  unsigned char* tca;
+  uint64_t* tcbar;
+  unsigned* tctm;
 };
 
 // Region k of a chunk ring, chosen with selects (a runtime index into the
@@ -267,6 +278,21 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   s.reg[0] = m.reg[0];
   s.reg[1] = m.reg[1];
   s.reg[2] = m.reg[2];
+  m.tcb = m.tca = nullptr;
+  m.tcbar = nullptr;
+  m.tctm = nullptr;
+  if (SP.tc) {
+    // operands start on 128-byte boundaries (16 bytes would do)
+    const uintptr_t a = (uintptr_t)(base + off);
+    off += ((a + 127) & ~(uintptr_t)127) - a;
+    const int nsp = SP.tc == TC_TF32X3 ? TcShape<TC_TF32X3>::NSPLIT : TcShape<TC_BF16X3>::NSPLIT;
+    const int bb = SP.tc == TC_TF32X3 ? TcShape<TC_TF32X3>::B_BYTES : TcShape<TC_BF16X3>::B_BYTES;
+    const int ab = SP.tc == TC_TF32X3 ? TcShape<TC_TF32X3>::A_BYTES : TcShape<TC_BF16X3>::A_BYTES;
+    m.tcb = take((size_t)SHORT_TC_MAXG * nsp * bb);
+    m.tca = take((size_t)2 * nsp * ab);
+    m.tcbar = (uint64_t*)take(2 * sizeof(uint64_t));
+    m.tctm = (unsigned*)take(16);
+  }
   s.end = off;
   return m;
 }
@@ -597,7 +623,10 @@ __device__ __forceinline__ int swz(int R, int w) { return R * 16 + ((((w >> 1) ^
 // a launch's last kinetic substep).  TMA: chunks move by tensor copies (FP32,
 // 16-point axes; group 0 swizzled, other groups [plane][row][w]); else by
 // cp.async into the padded plane layout.
-template <typename T, int N, bool INV, int MODE, bool POST, bool TMA>
+// TCM: the line DFTs run on the tensor cores (mg_tc.cuh; FP32, 16-point
+// lines, TMA copies only), with the lines' pre- and post-multipliers folded
+// into the DFT matrix; TC_NONE: register DFTs.
+template <typename T, int N, bool INV, int MODE, bool POST, bool TMA, int TCM>
 __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, const Bufs& B,
                                        const SSm<typename VT<T>::v, T>& Sref, int gi, int slot) {
   constexpr int mode = MODE;
@@ -619,6 +648,30 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   unsigned parity = TMA ? *S.s.mphase : 0u;
   LineAcc<T> acc;
   acc.zero();
+  unsigned tmem = 0, tcpar = 0;
+  if constexpr (TCM != TC_NONE && MODE != SM_VONLY) {
+    static_assert(sizeof(T) == 4 && N == 16 && TMA, "tensor-core DFTs: FP32, 16-point lines, TMA copies");
+    using TS = TcShape<TCM>;
+    // DFT matrices of the group's axes with their multipliers folded in:
+    // forward A_l (or the relative demodulation), inverse K_l, and conj(A_l)
+    // after the inverse DFT of a launch's last kinetic substep
+    for (int k = 0; k < g; ++k) {
+      const int a = l0 + k;
+      tc_build_b<TCM, INV>(S.tcb + k * TS::NSPLIT * TS::B_BYTES, (INV ? S.s.tK : S.s.tA) + a * N,
+                           (INV && POST) ? S.s.tAi + a * N : nullptr);
+    }
+    if (threadIdx.x == 0) {
+      mbar_init(S.tcbar);
+      mbar_init(S.tcbar + 1);
+      fence_mbar_init();
+    }
+    fence_proxy_async();  // B operands written by threads, read by the tensor cores
+    tc_alloc(S.tctm);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = *S.tctm;
+  }
 
   // A "set" is the chunk(s) transformed together: one chunk, or two for FP64
   // 12-point lines (see short_lpc), whose regions rotate X, Y (set) and Z
@@ -698,9 +751,14 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       // element addressing: linear (base + r * stride) except for the swizzled
       // layout along its last two axes
       const int kind = (lay == 1 && k == g - 1) ? 2 : ((lay == 1 && k == g - 2) ? 1 : 0);
-      for (int Lset = threadIdx.x; Lset < nl; Lset += blockDim.x) {
-        const int hs = Lset >= nls[0];
-        const int L = Lset - (hs ? nls[0] : 0);
+      // tensor-core DFTs: every thread of a warpgroup takes part in every
+      // round (one line each, or an empty row)
+      const int nrounds = (nl + blockDim.x - 1) / blockDim.x;
+      for (int Lset = threadIdx.x, rr = 0; TCM != TC_NONE ? rr < nrounds : Lset < nl; Lset += blockDim.x, ++rr) {
+        const bool have = TCM == TC_NONE || Lset < nl;
+        const int Lc = have ? Lset : 0;
+        const int hs = Lc >= nls[0];
+        const int L = Lc - (hs ? nls[0] : 0);
         V* reg = regs[hs];
         const unsigned cbase = cbs[hs];
         int wt, hi, lo, base = 0, stride = 0;
@@ -727,7 +785,10 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           }
         }
         V x[N];
-        if (kind == 0) {
+        if (!have) {
+#pragma unroll
+          for (int r = 0; r < N; ++r) x[r] = V{(T)0, (T)0};
+        } else if (kind == 0) {
 #pragma unroll
           for (int r = 0; r < N; ++r) x[r] = reg[base + r * stride];
         } else if (kind == 1) {  // rows R = (wt*16 + hi)*16 + r, word lo
@@ -743,13 +804,34 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
             x[2 * cp + 1] = V{(T)v2.z, (T)v2.w};
           }
         }
+        if constexpr (TCM != TC_NONE) {
+          // the line as row `row` of its warpgroup's A operand; one thread
+          // issues the split products, all wait for them and read their row
+          using TS = TcShape<TCM>;
+          const int wg = threadIdx.x >> 7, row = threadIdx.x & 127;
+          unsigned char* ab = S.tca + wg * TS::NSPLIT * TS::A_BYTES;
+          tc_stage_line<TCM>(ab, row, reinterpret_cast<const float2*>(x));
+          fence_proxy_async();
+          tc_named_sync(1 + wg, 128);
+          if (row == 0) tc_issue<TCM>(tmem + wg * 32, ab, S.tcb + k * TS::NSPLIT * TS::B_BYTES, S.tcbar + wg);
+          wait_chunk(B, S.tcbar + wg, tcpar);
+          tcpar ^= 1u;
+          tc_fence_after();
+          float v[32];
+          tc_ld32(tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + wg * 32, v);
+          tc_fence_before();
 #pragma unroll
-        for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
-        LineDft<INV, N, V>::run(x, tw);
-        if (post) {
+          for (int r = 0; r < N; ++r) x[r] = V{(T)v[2 * r], (T)v[2 * r + 1]};
+        } else {
 #pragma unroll
-          for (int r = 0; r < N; ++r) x[r] = cmul(x[r], post[r]);
+          for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
+          LineDft<INV, N, V>::run(x, tw);
+          if (post) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) x[r] = cmul(x[r], post[r]);
+          }
         }
+        if (!have) continue;
         if (last && mode == SM_KIN) {
           // kinetic moments; the line runs along axis 0 (k = 0, l0 = 0)
           int j[MAXD];
@@ -890,6 +972,12 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   } else {
     cp_wait<0>();
   }
+  if constexpr (TCM != TC_NONE && MODE != SM_VONLY) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tc_dealloc(tmem);
+  }
   if (MODE != SM_NONE) block_record<T>(B, S.s.red, slot, acc, D + 1);
 }
 
@@ -897,7 +985,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
 // The persistent kernel
 // ---------------------------------------------------------------------------
 
-template <typename T, int N, bool TMA>
+template <typename T, int N, bool TMA, int TCM>
 __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     k_propagate_short(const __grid_constant__ Plan P, const __grid_constant__ Bufs B,
                       const __grid_constant__ Run RN, const __grid_constant__ ShortPlan SP) {
@@ -938,7 +1026,7 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     if (!grid_sync(B, &sflag)) return;
     load_v_short(P, SP, B, S);
     __syncthreads();
-    short_pass<T, N, false, SM_VONLY, false, TMA>(P, SP, B, S, 0, 1);
+    short_pass<T, N, false, SM_VONLY, false, TMA, TCM>(P, SP, B, S, 0, 1);
     if (!grid_sync(B, &sflag)) return;
     finish(B, S.s, 1, D + 1);
     centre_after_potential(P, S.s, RN.motion);
@@ -965,8 +1053,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     // forward transform, group by group from the last axis; kinetic moments
     // in the pass over the group that holds axis 0
     for (int gi = 0; gi < ng; ++gi) {
-      if (gi == ng - 1) short_pass<T, N, false, SM_KIN, false, TMA>(P, SP, B, S, gi, 0);
-      else short_pass<T, N, false, SM_NONE, false, TMA>(P, SP, B, S, gi, 0);
+      if (gi == ng - 1) short_pass<T, N, false, SM_KIN, false, TMA, TCM>(P, SP, B, S, gi, 0);
+      else short_pass<T, N, false, SM_NONE, false, TMA, TCM>(P, SP, B, S, gi, 0);
       if (!grid_sync(B, &sflag)) return;
     }
     finish(B, S.s, 0, D + 1);
@@ -984,11 +1072,11 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     for (int gi = ng - 1; gi >= 0; --gi) {
       const bool v = (gi == 0 && hasv);
       if (final_unit) {
-        if (v) short_pass<T, N, true, SM_V, true, TMA>(P, SP, B, S, gi, 1);
-        else short_pass<T, N, true, SM_NONE, true, TMA>(P, SP, B, S, gi, 1);
+        if (v) short_pass<T, N, true, SM_V, true, TMA, TCM>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, true, TMA, TCM>(P, SP, B, S, gi, 1);
       } else {
-        if (v) short_pass<T, N, true, SM_V, false, TMA>(P, SP, B, S, gi, 1);
-        else short_pass<T, N, true, SM_NONE, false, TMA>(P, SP, B, S, gi, 1);
+        if (v) short_pass<T, N, true, SM_V, false, TMA, TCM>(P, SP, B, S, gi, 1);
+        else short_pass<T, N, true, SM_NONE, false, TMA, TCM>(P, SP, B, S, gi, 1);
       }
       if (gi > 0 && !grid_sync(B, &sflag)) return;
     }
@@ -1028,20 +1116,38 @@ done:
 
 // The kernel for FP64 (prec 0) or FP32 (prec 1) storage and axis length n;
 // tma: the chunk copies use TMA tensor maps (FP32, n = 16 only).
-void* short_kernel(int prec, int n, int tma) {
-  if (tma) return (prec == 1 && n == 16) ? (void*)k_propagate_short<float, 16, true> : nullptr;
+// tc: the line DFTs on the tensor cores (TC_TF32X3 / TC_BF16X3; FP32, n = 16
+// with TMA only).
+void* short_kernel(int prec, int n, int tma, int tc) {
+  if (tma) {
+    if (prec != 1 || n != 16) return nullptr;
+    if (tc == TC_TF32X3) return (void*)k_propagate_short<float, 16, true, TC_TF32X3>;
+    if (tc == TC_BF16X3) return (void*)k_propagate_short<float, 16, true, TC_BF16X3>;
+    return tc ? nullptr : (void*)k_propagate_short<float, 16, true, TC_NONE>;
+  }
+  if (tc) return nullptr;
   switch (n * 2 + prec) {
-    case 16: return (void*)k_propagate_short<double, 8, false>;
-    case 17: return (void*)k_propagate_short<float, 8, false>;
-    case 24: return (void*)k_propagate_short<double, 12, false>;
-    case 25: return (void*)k_propagate_short<float, 12, false>;
-    case 32: return (void*)k_propagate_short<double, 16, false>;
-    case 33: return (void*)k_propagate_short<float, 16, false>;
+    case 16: return (void*)k_propagate_short<double, 8, false, TC_NONE>;
+    case 17: return (void*)k_propagate_short<float, 8, false, TC_NONE>;
+    case 24: return (void*)k_propagate_short<double, 12, false, TC_NONE>;
+    case 25: return (void*)k_propagate_short<float, 12, false, TC_NONE>;
+    case 32: return (void*)k_propagate_short<double, 16, false, TC_NONE>;
+    case 33: return (void*)k_propagate_short<float, 16, false, TC_NONE>;
   }
   return nullptr;
 }
 
 int short_threads_for(int prec, int n) { return short_threads(prec, n); }
-int short_lpc_for(int prec, int n) { return short_lpc(prec, n); }
+int short_lpc_for(int prec, int n, int tc) { return short_lpc_tc(prec, n, tc); }
+// Shared-memory bytes of the tensor-core operands (carve_short, with its
+// 128-byte alignment): B operands of up to 3 axes, A operands of two
+// warpgroups, two mbarriers, the TMEM address slot.
+int short_tc_smem_bytes(int tc) {
+  if (!tc) return 0;
+  const int nsp = tc == TC_TF32X3 ? TcShape<TC_TF32X3>::NSPLIT : TcShape<TC_BF16X3>::NSPLIT;
+  const int bb = tc == TC_TF32X3 ? TcShape<TC_TF32X3>::B_BYTES : TcShape<TC_BF16X3>::B_BYTES;
+  const int ab = tc == TC_TF32X3 ? TcShape<TC_TF32X3>::A_BYTES : TcShape<TC_BF16X3>::A_BYTES;
+  return 128 + SHORT_TC_MAXG * nsp * bb + 2 * nsp * ab + 16 + 16;
+}
 
 }  // namespace mgk

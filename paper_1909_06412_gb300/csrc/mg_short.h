@@ -17,7 +17,8 @@
 
 namespace mgk {
 
-constexpr int SHORT_MAXG = 4;  // axes per group
+constexpr int SHORT_MAXG = 4;     // axes per group
+constexpr int SHORT_TC_MAXG = 3;  // axes per group of the tensor-core variant (TMA plans)
 
 // One group of consecutive axes l0 .. l0+g-1 and how its passes are chunked.
 //  - contig = 1: the group ends at the last (contiguous) axis; a chunk is WT
@@ -51,6 +52,7 @@ struct alignas(64) TensorMapBytes {
 struct ShortPlan {
   int on;            // the grid has the short-axis shape and the kernel fits
   int tma;           // chunks move by TMA tensor copies (FP32, n = 16); else cp.async
+  int tc;            // line DFTs on the tensor cores: 0 none, 1 3xTF32, 2 BF16x3 (FP32, n = 16, TMA)
   int trank[MAXD];   // rank of each group's tensor map
   int n;             // axis length
   int ngroups;       // grp[0] ends at the last axis, grp[ngroups-1] starts at axis 0

@@ -251,3 +251,45 @@ def test_gradient_3d_harmonic_vs_finite_differences(mg):
     fd["s"] = (J_of(q0n, p0n, 1.0 + h) - J_of(q0n, p0n, 1.0 - h)) / (2 * h)
     for name in fd:
         assert abs(grads[name] - fd[name]) < 1e-6 * max(1.0, abs(fd[name])), (name, grads[name], fd[name])
+
+
+def test_autograd_two_forwards_before_their_backwards(mg):
+    # One context, two forward passes with different potentials and start
+    # centres before either backward, then each backward (the second one twice,
+    # through a retained graph).  Each gradient must match the oracle's taped
+    # gradient of its own forward pass: the backward restores the end state of
+    # its forward pass into the context before the reversible adjoint runs.
+    from paper_1909_06412_gb300.autograd import MovingGridPropagate
+
+    N, dq = (48, 36), (0.4, 0.25)
+    g, _, pot = atom_diatom_pair(mg, N, dq)
+    ubase = g.psi.view(torch.complex128).clone().reshape(N)
+    _, qbase, pbase, _ = g.get_state(want_psi=False)
+    cell = np.sqrt(np.prod(dq))
+    c = torch.from_numpy(inputs.random_state(N, seed=8) * 0.5).to(g.device)
+    cases = [(np.array([P["Dm"], P["a"], P["beta"], P["A"]]), 0.0),
+             (np.array([P["Dm"] * 1.1, P["a"] * 0.95, P["beta"] * 1.05, P["A"] * 0.9]), 0.25)]
+    runs = []
+    for theta, shift in cases:
+        u0 = ubase.clone().requires_grad_(True)
+        q0t = torch.tensor(qbase + np.array([shift, 0.0]), requires_grad=True)
+        p0t = torch.tensor(pbase, requires_grad=True)
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        uT, qT, pT = MovingGridPropagate.apply(u0, q0t, p0t, th, g, 5, 2.0, "yoshida4")
+        L = (torch.conj(c) * uT).real.sum() + qT[0] * 0.3 - pT[1] * 0.2
+        runs.append((L, (u0, q0t, p0t, th), theta, shift))
+    for k in (1, 0, 1):
+        L, leaves, theta, shift = runs[k]
+        gu, gq, gp, gth = torch.autograd.grad(L, leaves, retain_graph=True)
+        Dm, a, be, A = theta
+        o = oracle.Grid(N, dq, minv=(1 / P["mu"][0], 1 / P["mu"][1]))
+        pot_k = [Dm, a, P["re"], A, be]
+        o.set_potential(oracle.POT_ATOM_DIATOM, pot_k)
+        o.set_state(ubase.cpu().numpy() / cell, qbase + np.array([shift, 0.0]), pbase)
+        tape = Tape(o, oracle.POT_ATOM_DIATOM, pot_k)
+        tape.run(5, 2.0, "yoshida4")
+        ubo, qbo, pbo, tho = tape.backward(c.cpu().numpy(), np.array([0.3, 0.0]), np.array([0.0, -0.2]))
+        assert rel(gu.cpu().numpy(), ubo) < 1e-9, k
+        assert np.allclose(gq.numpy(), qbo, rtol=1e-9, atol=1e-10), k
+        assert np.allclose(gp.numpy(), pbo, rtol=1e-9, atol=1e-10), k
+        assert np.allclose(gth.numpy(), tho, rtol=1e-8, atol=1e-10), k

@@ -103,7 +103,7 @@ def test_batch_fp64_matches_oracle(mg, cluster):
         psi, q, p, t = state(g)
         psi_o, q_o, p_o, t_o = o.get_state()
         assert rel(psi, psi_o) < 1e-12, pr["N"]
-        assert np.allclose(q, q_o, rtol=0, atol=1e-12) and np.allclose(p, p_o, rtol=0, atol=1e-11)
+        assert np.allclose(q, q_o, rtol=1e-12, atol=1e-12) and np.allclose(p, p_o, rtol=1e-12, atol=1e-12)
         assert abs(t - steps * pr["dt"]) < 1e-12
 
 
@@ -120,7 +120,7 @@ def test_batch_splits_and_grid_motion(mg, split, motion):
         psi, q, p, _ = state(g)
         psi_o, q_o, p_o, _ = o.get_state()
         assert rel(psi, psi_o) < 1e-12
-        assert np.allclose(q, q_o, atol=1e-12) and np.allclose(p, p_o, atol=1e-11)
+        assert np.allclose(q, q_o, rtol=1e-12, atol=1e-12) and np.allclose(p, p_o, rtol=1e-12, atol=1e-12)
 
 
 def test_batch_fp32_matches_oracle(mg):
@@ -153,7 +153,7 @@ def test_batch_matches_single_grid_path_on_the_seeded_workload(mg):
         psi, q, p, _ = state(g)
         psi_s, q_s, p_s, _ = state(s)
         assert rel(psi, psi_s) < 1e-12, pr["N"]
-        assert np.allclose(q, q_s, atol=1e-12) and np.allclose(p, p_s, atol=1e-11)
+        assert np.allclose(q, q_s, rtol=1e-12, atol=1e-12) and np.allclose(p, p_s, rtol=1e-12, atol=1e-12)
         s.close()
 
 
@@ -225,7 +225,7 @@ def test_batch_picks_up_potential_changes(mg):
     o.propagate(2, probs[0]["dt"], "strang")
     psi, q, p, _ = state(gs[0])
     psi_o, q_o, p_o, _ = o.get_state()
-    assert rel(psi, psi_o) < 1e-12 and np.allclose(p, p_o, atol=1e-11)
+    assert rel(psi, psi_o) < 1e-12 and np.allclose(p, p_o, rtol=1e-12, atol=1e-12)
 
 
 def test_batch_reports_the_failed_problem(mg):

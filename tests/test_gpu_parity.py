@@ -46,7 +46,7 @@ def assert_same(g, o, tol=TOL):
     sq = max(1.0, np.abs(q_o).max())
     sp = max(1.0, np.abs(p_o).max())
     assert np.abs(q - q_o).max() < tol * sq, (q, q_o)
-    assert np.abs(p - p_o).max() < tol * sp * 10, (p, p_o)
+    assert np.abs(p - p_o).max() < tol * sp, (p, p_o)
     return err
 
 
@@ -103,11 +103,15 @@ def test_atom_diatom_full_grid_yoshida4(mg):
     assert_same(g, o)
 
 
-@pytest.mark.parametrize("scheme", ["strang", "yoshida4", "suzuki4", "yoshida6", "yoshida8"])
-def test_atom_diatom_schemes(mg, scheme):
+@pytest.mark.parametrize("scheme,steps", [("strang", 12), ("yoshida4", 12), ("suzuki4", 12), ("yoshida6", 12),
+                                          ("yoshida8", 12), ("yoshida10", 6), ("suzuki6", 12), ("suzuki8", 4),
+                                          ("suzuki10", 2)])
+def test_atom_diatom_schemes(mg, scheme, steps):
+    # every composition the library offers, up to tenth order (81 and 625
+    # stages per step for yoshida10 and suzuki10)
     g, o = atom_diatom(mg, (64, 48), (0.32, 0.2))
-    g.propagate(12, 2.0, scheme)
-    o.propagate(12, 2.0, scheme)
+    g.propagate(steps, 2.0, scheme)
+    o.propagate(steps, 2.0, scheme)
     assert_same(g, o)
 
 
@@ -208,7 +212,7 @@ def test_observables_match_oracle(mg):
     n, e, mq, mp = g.observables()
     no, eo, mqo, mpo = o.observables()
     assert abs(n - no) < 1e-13 and abs(e - eo) < 1e-12 * abs(eo)
-    assert np.allclose(mq, mqo, rtol=1e-12, atol=1e-12) and np.allclose(mp, mpo, rtol=1e-12, atol=1e-11)
+    assert np.allclose(mq, mqo, rtol=1e-12, atol=1e-12) and np.allclose(mp, mpo, rtol=1e-12, atol=1e-12)
 
 
 def test_reversibility_and_norm_on_gpu(mg):
@@ -273,3 +277,23 @@ def test_argument_errors(mg):
         g.propagate(1, 0.1, "yoshida5")
     with pytest.raises(mg.MgError):
         g.set_potential(mg.MG_POT_ATOM_DIATOM, [1.0, 2.0])
+
+
+def test_host_buffer_upload_and_download(mg):
+    # mg_upload_u / mg_download_u move the scaled state without conversion;
+    # a propagation between them matches the oracle
+    g, o = atom_diatom(mg, (64, 48), (0.32, 0.2))
+    u = g.psi.view(torch.complex128).cpu().pin_memory()
+    _, q0, p0, _ = g.get_state(want_psi=False)
+    g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 2, [0.0, 0.0], [0.0, 0.0])  # overwritten below
+    g.upload_u(u, q0, p0, 0.0)
+    g.propagate(10, 2.0, "yoshida4")
+    o.propagate(10, 2.0, "yoshida4")
+    out = torch.empty_like(u).pin_memory()
+    q, p, t = g.download_u(out)
+    psi_o, q_o, p_o, _ = o.get_state()
+    cell = np.sqrt(0.32 * 0.2)
+    assert rel(out.numpy().reshape(64, 48) / cell, psi_o) < TOL
+    assert np.abs(q - q_o).max() < TOL * max(1.0, np.abs(q_o).max())
+    assert np.abs(p - p_o).max() < TOL * max(1.0, np.abs(p_o).max())
+    assert abs(t - 20.0) < 1e-12

@@ -1,0 +1,48 @@
+"""The device arithmetic the kernels rely on, checked directly.
+
+- The table-driven e^{i theta} of the kernels (Tang's method: a three-word
+  Cody-Waite reduction by pi/128, a 256-entry table, short Taylor series)
+  against the host's sin and cos over the argument range the phase factors
+  reach (|theta| up to 1e5 rad at the grid edges of the atom-diatom model),
+  with a stated bound: at most 2 ulp of 1.0 (4.4e-16) absolute.
+- The FMA rate probe that the benchmark's FP64 roofline is stated against.
+"""
+import numpy as np
+import pytest
+
+from tests import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1909_06412_gb300 as m
+
+    m.lib()
+    return m
+
+
+def test_table_sincos_against_host(mg):
+    g = inputs.rng(77)
+    th = np.concatenate([
+        g.uniform(-1e5, 1e5, 400000), g.uniform(-10.0, 10.0, 400000), g.uniform(-1e-3, 1e-3, 50000),
+        np.arange(-512, 513) * (np.pi / 128),  # table nodes and their neighbours
+        np.nextafter(np.arange(-512, 513) * (np.pi / 128), np.inf),
+        np.arange(-600, 601) * (np.pi / 256),  # midpoints between nodes (largest |r|)
+        [0.0, -0.0, 1e-300, 3.0e7, -4.0e8],
+    ])
+    s, c = mg.mg_probe_expi(torch.from_numpy(th).cuda())
+    s, c = s.cpu().numpy(), c.cpu().numpy()
+    err = max(np.abs(s - np.sin(th)).max(), np.abs(c - np.cos(th)).max())
+    assert err <= 2.0 ** -51, err
+    assert np.abs(s * s + c * c - 1).max() < 1e-15
+
+
+def test_fma_rate_probe(mg):
+    r64 = mg.mg_probe_fma_rate(mg.MG_FP64)
+    r32 = mg.mg_probe_fma_rate(mg.MG_FP32_MIXED)
+    assert r64 > 0 and r32 > r64
