@@ -67,9 +67,11 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     minv = np.eye(2).ravel()
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(minv), 1.0, 0, None, None, 0, None) == -1
-    bad = np.array([[1.0, 0.2], [0.2, 1.0]]).ravel()
     fake = ctypes.c_void_p(256)
-    assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(bad), 1.0, 0, fake, fake, 1 << 30, None) == -2
+    # the inverse mass matrix must be symmetric positive definite (eq:KE_operator)
+    for bad in ([[1.0, 0.2], [0.3, 1.0]], [[1.0, 2.0], [2.0, 1.0]], [[0.0, 0.0], [0.0, 1.0]]):
+        bad = np.array(bad).ravel()
+        assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(bad), 1.0, 0, fake, fake, 1 << 30, None) == -1
     assert lib.mg_create(ctypes.byref(h), 2, p(N), p(dq), p(minv), -1.0, 0, fake, fake, 1 << 30, None) == -1
 
 
