@@ -235,6 +235,14 @@ def oracle_all_cores(D):
 
 
 def cpu_model():
+    """The host CPU's model name (lscpu), else what /proc/cpuinfo names."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part")):

@@ -79,8 +79,12 @@ enum { MG_POT_HARMONIC = 0, MG_POT_ATOM_DIATOM = 1, MG_POT_HENON_HEILES = 2,
 size_t mg_workspace_bytes(int D, const int64_t* N, int precision);
 
 /* Create a context (Sec. II.B grid; eq:KE_operator kinetic energy).
- * minv: D*D row-major inverse mass matrix; only diagonal matrices are
- * supported (MG_ERR_UNSUPPORTED otherwise).  d_psi: device buffer of
+ * minv: D*D row-major inverse mass matrix, symmetric positive definite
+ * (MG_ERR_ARG otherwise).  A matrix with off-diagonal entries runs on the
+ * general kernel, whose kinetic substep applies the non-separable part of
+ * e^{-i tau T(p^K)/hbar} point by point and moves the grid by
+ * tau m^-1 <p> with the full matrix; mg_adjoint and mg_batch_create refuse
+ * such contexts (MG_ERR_UNSUPPORTED).  d_psi: device buffer of
  * prod(N) complex elements of the chosen precision.  d_work: device buffer of
  * at least mg_workspace_bytes() bytes.  cuda_stream: a cudaStream_t (NULL =
  * legacy default stream).  The context keeps the pointers, not copies. */

@@ -248,7 +248,7 @@ bool short_plan(const Plan& P, ShortPlan& SP, int tc = 0) {
   SP.tc = tc;
   const int D = P.D;
   const int n = short_shape(D, P.N);
-  if (!n) return false;
+  if (!n || P.minv_general) return false;  // per-axis kinetic tables only
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const int threads = short_threads_for(P.prec, n);
   const int lpc = short_lpc_for(P.prec, n, tc);
@@ -462,7 +462,16 @@ void round_unit_f32_host(double x, double y, double* ox, double* oy) {
     }
 }
 
-// e^{i k pi/128}, k = 0..255, for the table-driven sincos of the kernels.
+}  // namespace
+
+namespace mgk {
+
+// e^{i k pi/128}, k = 0..255, for the table-driven sincos of the kernels:
+// cosine and sine of the extended-precision angle, each correctly rounded.
+// (Constants chosen to make |w| = 1 to the last bit instead move their
+// angles by up to an ulp; on the 256 x 256 atom-diatom run to t = 2000 a.u.
+// that took the p-centre 1e-12 further from an extended-precision run of the
+// method, while fixing only a norm drift of the same size.)
 void fill_sincos_table(double* t) {
   for (int k = 0; k < 256; ++k) {
     const long double a = 3.14159265358979323846264338327950288L * (long double)k / 128.0L;
@@ -470,6 +479,25 @@ void fill_sincos_table(double* t) {
     t[2 * k + 1] = (double)std::sin(a);
   }
 }
+
+// Forward twiddles e^{-2 pi i m / n}, m = 0 .. n-1, into t (2 n doubles):
+// correctly rounded FP64 pairs, or for FP32 storage the float pairs of
+// round_unit_f32_host.
+void fill_twiddles(int n, int prec, double* t);
+
+}  // namespace mgk
+
+void mgk::fill_twiddles(int n, int prec, double* t) {
+  for (int m = 0; m < n; ++m) {
+    const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
+    const double c = (double)std::cos(ang), s = (double)std::sin(ang);
+    t[2 * m] = c;
+    t[2 * m + 1] = -s;
+    if (prec) round_unit_f32_host(c, -s, &t[2 * m], &t[2 * m + 1]);
+  }
+}
+
+namespace {
 
 // ---- digamma by recurrence + asymptotic series (Abramowitz & Stegun 6.3.5,
 // ---- 6.3.18) for the Morse-state mean ------------------------------------------
@@ -607,13 +635,27 @@ mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, 
     if (!(dq[l] > 0) || !std::isfinite(dq[l])) return MG_ERR_ARG;
     if (!axis_supported(N[l])) return MG_ERR_UNSUPPORTED;
   }
-  for (int a = 0; a < D; ++a)
-    for (int b = 0; b < D; ++b) {
-      const double v = minv[a * D + b];
-      if (!std::isfinite(v)) return MG_ERR_ARG;
-      if (a != b && v != 0.0) return MG_ERR_UNSUPPORTED;
-      if (a == b && !(v > 0)) return MG_ERR_ARG;
-    }
+  // the inverse mass matrix of eq:KE_operator: symmetric positive definite
+  // (Cholesky factorisation succeeds)
+  {
+    double L[MAXD * MAXD] = {0};
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        const double v = minv[a * D + b];
+        if (!std::isfinite(v) || v != minv[b * D + a]) return MG_ERR_ARG;
+      }
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double s = minv[a * D + b];
+        for (int k = 0; k < b; ++k) s -= L[a * MAXD + k] * L[b * MAXD + k];
+        if (a == b) {
+          if (!(s > 0)) return MG_ERR_ARG;
+          L[a * MAXD + a] = std::sqrt(s);
+        } else {
+          L[a * MAXD + b] = s / L[b * MAXD + b];
+        }
+      }
+  }
   if (((uintptr_t)d_work & 255) || ((uintptr_t)d_psi & 15)) return MG_ERR_ARG;
   Layout L = layout_for(D, N, precision);
   if (work_bytes < L.total) return MG_ERR_ARG;
@@ -646,6 +688,11 @@ mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, 
     P.maxn = std::max(P.maxn, ax.n);
     radix_plan(ax.n, ax);
   }
+  for (int a = 0; a < D; ++a)
+    for (int b = 0; b < D; ++b) {
+      P.minvf[a * D + b] = minv[a * D + b];
+      if (a != b && minv[a * D + b] != 0.0) P.minv_general = 1;
+    }
   // grid of the persistent kernel: one CTA per SM (all co-resident)
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -723,15 +770,8 @@ mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, 
   std::vector<double> tw(2 * P.tab_total), kc(P.tab_total);
   for (int l = 0; l < D; ++l) {
     const int n = P.ax[l].n;
-    for (int m = 0; m < n; ++m) {
-      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
-      tw[2 * (P.ax[l].toff + m)] = (double)std::cos(ang);
-      tw[2 * (P.ax[l].toff + m) + 1] = -(double)std::sin(ang);
-      if (P.prec)
-        round_unit_f32_host(tw[2 * (P.ax[l].toff + m)], tw[2 * (P.ax[l].toff + m) + 1],
-                            &tw[2 * (P.ax[l].toff + m)], &tw[2 * (P.ax[l].toff + m) + 1]);
-      kc[P.ax[l].toff + m] = (double)(m - n / 2);
-    }
+    fill_twiddles(n, P.prec, &tw[2 * P.ax[l].toff]);
+    for (int m = 0; m < n; ++m) kc[P.ax[l].toff + m] = (double)(m - n / 2);
   }
   std::vector<double> sct(512);
   fill_sincos_table(sct.data());
@@ -1177,7 +1217,7 @@ mg_status mg_adjoint(mg_ctx* c, int64_t n_steps, double dt, const char* scheme, 
   if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
   const Plan& P = c->P;
   const int nth = P.pot_kind == MG_POT_ATOM_DIATOM ? 4 : 0;
-  if (P.prec != MG_FP64 || !P.resident) return MG_ERR_UNSUPPORTED;
+  if (P.prec != MG_FP64 || !P.resident || P.minv_general) return MG_ERR_UNSUPPORTED;
   if (P.pot_kind != MG_POT_HARMONIC && P.pot_kind != MG_POT_ATOM_DIATOM) return MG_ERR_UNSUPPORTED;
   if (ntheta != nth || (nth > 0 && !theta_bar)) return MG_ERR_ARG;
   for (int a = 0; a < P.D; ++a)
@@ -1500,12 +1540,8 @@ extern "C" mg_status mg_propagate_noalloc(int D, const int64_t* N, const double*
   fill_sincos_table(sct);
   for (int l = 0; l < D; ++l) {
     const int n = P.ax[l].n;
-    for (int m = 0; m < n; ++m) {
-      const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
-      tw[2 * (P.ax[l].toff + m)] = (double)std::cos(ang);
-      tw[2 * (P.ax[l].toff + m) + 1] = -(double)std::sin(ang);
-      kc[P.ax[l].toff + m] = (double)(m - n / 2);
-    }
+    fill_twiddles(n, MG_FP64, &tw[2 * P.ax[l].toff]);
+    for (int m = 0; m < n; ++m) kc[P.ax[l].toff + m] = (double)(m - n / 2);
   }
   for (int a = 0; a < 8; ++a) {
     ctrl[a] = a < D ? q[a] : 0.0;
@@ -1712,7 +1748,7 @@ mg_status mg_batch_create(mg_batch** out, int nprob, mg_ctx* const* ctxs, int cl
     if (!c) return MG_ERR_ARG;
     if (!c->pot_set || !c->state_set) return MG_ERR_STATE;
     if (c->P.prec != prec || c->stream != ctxs[0]->stream) return MG_ERR_ARG;
-    if (c->P.D > BATCH_MAXD) return MG_ERR_UNSUPPORTED;
+    if (c->P.D > BATCH_MAXD || c->P.minv_general) return MG_ERR_UNSUPPORTED;
     if (tile_bytes && tile_bytes[i] < 0) return MG_ERR_ARG;
     if (radix_max && radix_max[i] != 0 && radix_max[i] != 2 && radix_max[i] != 4 && radix_max[i] != 8)
       return MG_ERR_ARG;

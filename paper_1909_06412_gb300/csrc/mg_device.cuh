@@ -326,7 +326,7 @@ __device__ bool grid_sync(const Bufs& B, int* sflag) {
 
 // scalar slots (doubles) in Smem::sc
 enum { SC_Q = 0, SC_P = 8, SC_QN = 16, SC_DELTA = 24, SC_TAU = 32, SC_SIG = 33, SC_SGH = 34, SC_HASV = 35,
-       SC_ERR = 36, SC_N = SCALARS };
+       SC_ERR = 36, SC_MOM = 64, SC_N = SCALARS };
 
 template <typename V> struct Smem {
   V* tw;        // twiddles, all axes (tab_total)
@@ -830,6 +830,23 @@ struct PassArgs {
   double* rec = nullptr;
 };
 
+// sum_{a<b} minv_ab p_a p_b at the p-grid point of multi-index idx (the
+// off-diagonal part of T(p^K) = p^T m^-1 p / 2, eq:KE_operator).
+template <int DM>
+__device__ __forceinline__ double kinetic_cross(const Plan& P, const double* tc, const double* sc, const int* idx) {
+  double pk[DM];
+#pragma unroll
+  for (int a = 0; a < DM; ++a)
+    if (a < P.D) pk[a] = fma(tc[P.ax[a].toff + idx[a]], P.dp[a], sc[SC_P + a]);
+  double e = 0.0;
+#pragma unroll
+  for (int a = 0; a < DM; ++a)
+#pragma unroll
+    for (int b = a + 1; b < DM; ++b)
+      if (b < P.D) e = fma(P.minvf[a * P.D + b] * pk[a], pk[b], e);
+  return e;
+}
+
 // s + c += x with Knuth's error-free two-sum (FP32).
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   const float t = s + x;
@@ -1050,6 +1067,7 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
                 acc[1 + a] = fma(S.tc[P.ax[a].toff + idx[a]], w2, acc[1 + a]);
                 if (A.red == RED_OBS_KIN) te += S.te[P.ax[a].toff + idx[a]];
               }
+            if (A.red == RED_OBS_KIN && P.minv_general) te += kinetic_cross<DM>(P, S.tc, S.sc, idx);
             if (A.red == RED_OBS_KIN) acc[D + 1] = fma(te, w2, acc[D + 1]);
           } else {
             double th, g[DM];
@@ -1080,6 +1098,30 @@ __device__ int axis_pass(const Plan& P, const Bufs& B, const PassArgs& A, const 
               acc[D + 1] = fma(th, w2, acc[D + 1]);
             }
           }
+        }
+      }
+      if (A.red == RED_KIN && P.minv_general) {
+        // the non-separable part of the kinetic phase e^{-i tau T(p^K)/hbar}
+        // (eq:U_T_tensor, T = p^T m^-1 p / 2): e^{-i tau sum_{a<b} minv_ab p_a p_b / hbar},
+        // applied while the state is in p-representation; the separable part
+        // and the grid shift are in the per-axis tables of the inverse passes
+        int idx[DM];
+#pragma unroll
+        for (int a = 0; a < DM; ++a)
+          if (a < D) idx[a] = S.li[(ti * W + w) * D + a];
+        idx[A.l] = j;
+        const double th = over_hbar(P, -S.sc[SC_TAU] * kinetic_cross<DM>(P, S.tc, S.sc, idx));
+        if constexpr (sizeof(T) == 8) {
+          double sn, cs;
+          expi_tab(th, S.sct, sn, cs);
+          v = V{fma(v.x, cs, -v.y * sn), fma(v.x, sn, v.y * cs)};
+        } else {
+          const double kk = rint(th * 0.15915494309189535);
+          double r = fma(-kk, 6.283185307179586, th);
+          r = fma(-kk, 2.4492935982947064e-16, r);
+          float sn, cs;
+          sincosf((float)r, &sn, &cs);
+          v = V{fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs)};
         }
       }
       if (A.keep) cur[e] = v;
@@ -1180,11 +1222,23 @@ template <typename V> __device__ void centre_after_kinetic(const Plan& P, const 
     const int a = threadIdx.x;
     double* sc = S.sc;
     int bad = 0;
+    double pi = 0.0, n = 0.0;
     if (a < P.D) {
-      const double n = S.fin[0];
-      const double pi = fma(P.dp[a], S.fin[1 + a] / n, sc[SC_P + a]);
-      const double mom = motion == GRID_ADAPTIVE ? pi : sc[SC_P + a];
-      const double delta = motion == GRID_FIXED ? 0.0 : sc[SC_TAU] * P.minv[a] * mom;
+      n = S.fin[0];
+      pi = fma(P.dp[a], S.fin[1 + a] / n, sc[SC_P + a]);
+      sc[SC_MOM + a] = motion == GRID_ADAPTIVE ? pi : sc[SC_P + a];
+    }
+    __syncwarp();
+    if (a < P.D) {
+      // delta = tau m^-1 <p> (eq:eom_qt_solution_case_III_T) with the full
+      // symmetric inverse mass matrix of eq:KE_operator when it has
+      // off-diagonal entries
+      double mdot = P.minv[a] * sc[SC_MOM + a];
+      if (P.minv_general) {
+        mdot = 0.0;
+        for (int b = 0; b < P.D; ++b) mdot = fma(P.minvf[a * P.D + b], sc[SC_MOM + b], mdot);
+      }
+      const double delta = motion == GRID_FIXED ? 0.0 : sc[SC_TAU] * mdot;
       if (!(n > 0) || !isfinite(n) || !isfinite(pi)) bad = ST_NONFINITE;
       else if (fabs(delta) > 10.0 * P.N[a] * P.dq[a]) bad = ST_UNSTABLE;
       sc[SC_DELTA + a] = delta;

@@ -47,7 +47,9 @@ struct Plan {
   int max_lines;         // most lines in one smem chunk (any axis)
   int64_t npts;
   int64_t N[MAXD];
-  double dq[MAXD], dp[MAXD], minv[MAXD], hbar;
+  double dq[MAXD], dp[MAXD], minv[MAXD], hbar;  // minv: diagonal of the inverse mass matrix
+  double minvf[MAXD * MAXD];  // the full symmetric inverse mass matrix, row-major D x D
+  int minv_general;           // minvf has nonzero off-diagonal entries (general kernel only)
   AxisPlan ax[MAXD];
   int pot_kind;
   int pot_general;       // harmonic potential with a non-diagonal K

@@ -19,6 +19,8 @@
 #include "mgrid.h"
 
 namespace mgk {
+void fill_sincos_table(double* t);  // mg_capi.cu: the contexts' table
+
 namespace {
 
 constexpr int FMA_CHAINS = 8;
@@ -107,10 +109,7 @@ extern "C" mg_status mg_probe_expi(const double* d_theta, double* d_sin, double*
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // e^{i k pi/128}, k = 0..255, exactly as the contexts build it
   double2 tab[256];
-  for (int k = 0; k < 256; ++k) {
-    const long double a = 3.14159265358979323846264338327950288L * (long double)k / 128.0L;
-    tab[k] = make_double2((double)std::cos(a), (double)std::sin(a));
-  }
+  fill_sincos_table(reinterpret_cast<double*>(tab));
   if (cudaMemcpyToSymbolAsync(g_expi_table, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return MG_ERR_CUDA;
   k_expi<<<1024, 256, 0, st>>>(d_theta, d_sin, d_cos, n);

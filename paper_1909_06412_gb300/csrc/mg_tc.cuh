@@ -111,19 +111,22 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 }
 
 // 32 consecutive f32 columns of this thread's TMEM lane (row), warp w of the
-// warpgroup reading lanes 32 (w % 4) .. 32 (w % 4) + 31.
+// warpgroup reading lanes 32 (w % 4) .. 32 (w % 4) + 31.  The load and its
+// wait are one asm statement: the destination registers of tcgen05.ld are
+// undefined until tcgen05.wait::ld, and a separate statement would let the
+// compiler copy or spill them in between.
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -194,7 +197,7 @@ template <int TC> __device__ __forceinline__ void tc_stage_line(unsigned char* a
 
 // The B operand parts of one axis: the 32 x 32 real form of
 // M[j][i] = post[j] W^{ji} pre[i], W = e^{-2 pi i/16} (e^{+2 pi i/16} for the
-// inverse), post = 1 when absent.  Work dealt over the CTA; the caller
+// inverse), pre and post = 1 when absent.  Work dealt over the CTA; the caller
 // synchronises (and fences the async proxy) before the MMAs read it.
 template <int TC, bool INV>
 __device__ void tc_build_b(unsigned char* bbase, const float2* pre, const float2* post) {
@@ -204,7 +207,7 @@ __device__ void tc_build_b(unsigned char* bbase, const float2* pre, const float2
     double sw, cw;
     sincospi((INV ? 2.0 : -2.0) * (double)((j * i) & 15) / 16.0, &sw, &cw);
     // m = post_j * w * pre_i in FP64 from the FP32 multipliers
-    const double pr = pre[i].x, pi = pre[i].y;
+    const double pr = pre ? pre[i].x : 1.0, pi = pre ? pre[i].y : 0.0;
     double mr = cw * pr - sw * pi, mi = cw * pi + sw * pr;
     if (post) {
       const double qr = post[j].x, qi = post[j].y;

@@ -297,3 +297,58 @@ def test_host_buffer_upload_and_download(mg):
     assert np.abs(q - q_o).max() < TOL * max(1.0, np.abs(q_o).max())
     assert np.abs(p - p_o).max() < TOL * max(1.0, np.abs(p_o).max())
     assert abs(t - 20.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# a full (non-diagonal) inverse mass matrix, eq:KE_operator (general kernel)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["harmonic3d", "henon_heiles3d_fixed", "atom_diatom"])
+def test_full_inverse_mass_matrix(mg, case):
+    if case == "atom_diatom":
+        P = inputs.ATOM_DIATOM
+        N, dq = (64, 48), (0.32, 0.2)
+        m = np.array([[1 / P["mu"][0], 0.2 / P["mu"][0]], [0.2 / P["mu"][0], 1 / P["mu"][1]]])
+        kind, pot = oracle.POT_ATOM_DIATOM, [P["Dm"], P["a"], P["re"], P["A"], P["beta"]]
+        rbar = oracle.morse_mean(P["Dm"], P["a"], P["re"], P["mu"][1])
+        fac = [("gauss", P["R0"], P["P0"], P["sigma"]), ("morse", P["Dm"], P["a"], P["re"], P["mu"][1])]
+        qc, pc, dt, steps, motion = [P["R0"], rbar], [P["P0"], 0.0], 2.0, 12, oracle.GRID_ADAPTIVE
+    else:
+        N, dq = (16, 20, 12), (0.5, 0.45, 0.6)
+        m = np.array([[1.0, 0.25, -0.1], [0.25, 0.8, 0.15], [-0.1, 0.15, 1.2]])
+        if case == "harmonic3d":
+            kind, pot = oracle.POT_HARMONIC, [1.0, 0, 0, 0, 1.44, 0, 0, 0, 2.25, 0.1, -0.2, 0.0]
+            motion = oracle.GRID_ADAPTIVE
+        else:
+            kind, pot = oracle.POT_HENON_HEILES, [inputs.HENON_HEILES["lam"]]
+            motion = oracle.GRID_FIXED
+        fac = [("gauss", 1.0, 0.3, 0.9), ("gauss", -0.5, -0.2, 0.8), ("gauss", 0.4, 0.1, 1.0)]
+        qc, pc, dt, steps = [1.0, -0.5, 0.4], [0.3, -0.2, 0.1], 0.05, 20
+    g, o = pair(mg, N, dq, m, kind, pot)
+    assert g.path == 0  # the short-axis kernel takes diagonal matrices only
+    g.set_separable(fac, qc, pc)
+    o.set_separable(fac, qc, pc)
+    g.propagate(steps, dt, "yoshida4", oracle.SPLIT_TVT, motion)
+    o.propagate(steps, dt, "yoshida4", oracle.SPLIT_TVT, motion)
+    assert_same(g, o)
+    n, e, mq, mp = g.observables()
+    no, eo, mqo, mpo = o.observables()
+    assert abs(n - no) < 1e-13 and abs(e - eo) < 1e-12 * abs(eo)
+    assert np.allclose(mp, mpo, rtol=1e-12, atol=1e-12)
+
+
+def test_full_inverse_mass_matrix_is_refused_where_unsupported(mg):
+    m = np.array([[1.0, 0.2, 0.0], [0.2, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    g = mg.Propagator((16, 16, 16), (0.5,) * 3, minv=m)
+    g.set_potential(mg.MG_POT_HARMONIC, [1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0, 0, 0, 0])
+    g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 3, [0, 0, 0], [0, 0, 0])
+    g.propagate(2, 0.05, "strang")
+    with pytest.raises(mg.MgError) as e:
+        g.adjoint(2, 0.05, "strang", np.zeros((16, 16, 16), complex), np.zeros(3), np.zeros(3))
+    assert e.value.code == mg.MG_ERR_UNSUPPORTED
+    with pytest.raises(mg.MgError) as e:
+        mg.Batch([g])
+    assert e.value.code == mg.MG_ERR_UNSUPPORTED
+    with pytest.raises(mg.MgError) as e:  # not symmetric
+        mg.Propagator((16, 16), (0.5, 0.5), minv=np.array([[1.0, 0.2], [0.1, 1.0]]))
+    assert e.value.code == mg.MG_ERR_ARG
