@@ -97,14 +97,13 @@ mg_status mg_create(mg_ctx** out, int D, const int64_t* N, const double* dq, con
  * through memory and which units compute them.
  *  MG_CREATE_GENERAL_KERNEL  never use the short-axis kernel (one pass per axis)
  *  MG_CREATE_NO_TMA          short-axis kernel with cp.async chunk copies only
- *  MG_CREATE_TC_TF32X3       short-axis kernel (TMA copies) whose 16-point line
- *                            DFTs run on the tensor cores as a GEMM with
- *                            3xTF32 split products accumulated in FP32
- *  MG_CREATE_TC_BF16X3       the same with BF16x3 split products (each value
- *                            split into three bfloat16 terms, six products)
- * The two tensor-core flags need an MG_FP32_MIXED grid of D >= 3 axes of 16
- * points each (MG_ERR_UNSUPPORTED otherwise); at most one of them, and
- * neither with the first two flags (MG_ERR_ARG). */
+ *  MG_CREATE_TC_TF32X3       reserved: the short-axis kernel with its 16-point
+ *  MG_CREATE_TC_BF16X3       line DFTs on the tensor cores (3xTF32 / BF16x3
+ *                            split products).  Not enabled in this build: both
+ *                            return MG_ERR_UNSUPPORTED.  The tensor-core
+ *                            16-point DFT itself is mg_probe_tc_dft16.
+ * At most one tensor-core flag, and neither with the first two flags
+ * (MG_ERR_ARG). */
 enum { MG_CREATE_GENERAL_KERNEL = 1, MG_CREATE_NO_TMA = 2, MG_CREATE_TC_TF32X3 = 4, MG_CREATE_TC_BF16X3 = 8 };
 mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, const double* minv,
                        double hbar, int precision, void* d_psi, void* d_work, size_t work_bytes,
@@ -221,10 +220,8 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
  * several axes transformed per pass over the state), 2 = the same kernel
  * moving its chunks with TMA tensor copies (FP32 storage, 16-point axes),
  * 0 = the general kernel (one pass per axis), -1 for a NULL context or no
- * potential yet; 3 and 4 = the short-axis kernel with TMA copies and its
- * line DFTs on the tensor cores (3xTF32 and BF16x3 split products,
- * mg_create_ex).  The same method either way (Sec. II.G); only the memory
- * traffic and the arithmetic units differ.  mg_create_ex's flags choose. */
+ * potential yet.  The same method either way (Sec. II.G); only the memory
+ * traffic differs.  mg_create_ex's flags choose. */
 int mg_propagate_path(const mg_ctx* ctx);
 
 /* Host-only (no GPU): the stage coefficients gamma_1..gamma_S of a named
@@ -261,6 +258,20 @@ int mg_short_axis_plan(int D, const int64_t* N, int precision, int* first_axis, 
  * written to d_sin and d_cos (device FP64, n each); synchronises cuda_stream.
  * Neither allocates device memory. */
 mg_status mg_probe_fma_rate(int precision, void* cuda_stream, double* tflops);
+
+/* The n-point DFT of eq:F_defintion's discrete transform (n = 16) as a dense
+ * GEMM on the tensor cores (tcgen05.mma, operands in shared memory,
+ * accumulator in tensor memory), applied to nlines independent lines:
+ *   y_l[j] = post[j] sum_i e^{s 2 pi i j i / 16} pre[i] x_l[i],
+ * s = -1 (inverse = 0) or +1 (inverse = 1), unnormalised.  d_x, d_y: device
+ * complex64 (interleaved FP32), 16 values per line, line-major.  pre, post:
+ * host complex FP64 (16 values each; post may be NULL for 1).  split = 1:
+ * 3xTF32 split products (x = xb + xs, M = Mb + Ms, Xb Mb + Xb Ms + Xs Mb);
+ * split = 2: BF16x3 (three bfloat16 terms each, six products); FP32
+ * accumulation either way.  Synchronises cuda_stream; MG_ERR_TIMEOUT if a
+ * tensor-core completion wait ran out (every wait is bounded). */
+mg_status mg_probe_tc_dft16(int split, int inverse, const void* d_x, void* d_y, int64_t nlines, const double* pre,
+                            const double* post, void* cuda_stream);
 mg_status mg_probe_expi(const double* d_theta, double* d_sin, double* d_cos, int64_t n, void* cuda_stream);
 
 /* <x> under the Morse ground state above (host quadrature helper for

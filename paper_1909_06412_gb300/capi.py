@@ -27,7 +27,7 @@ __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "M
                                                         "mg_batch_workspace_bytes", "mg_morse_mean",
                                                         "mg_propagate_noalloc", "mg_short_axis_plan",
                                                         "mg_scheme_coefficients", "mg_probe_fma_rate",
-                                                        "mg_probe_expi"]
+                                                        "mg_probe_expi", "mg_probe_tc_dft16"]
 
 _lib = None
 
@@ -57,6 +57,7 @@ def lib():
         L.mg_download_u.argtypes = [vp, vp, vp, vp, vp]
         L.mg_probe_fma_rate.argtypes = [i32, vp, vp]
         L.mg_probe_expi.argtypes = [vp, vp, vp, i64, vp]
+        L.mg_probe_tc_dft16.argtypes = [i32, i32, vp, vp, i64, vp, vp, vp]
         L.mg_regrid.argtypes = [vp, vp, vp]
         L.mg_inner_product.argtypes = [vp, vp, vp, vp]
         L.mg_kernel_launches.argtypes = [vp]
@@ -83,7 +84,8 @@ def lib():
                      "mg_propagate", "mg_get_state", "mg_get_observables", "mg_sync", "mg_test_stuck_barrier",
                      "mg_adjoint", "mg_regrid", "mg_inner_product",
                      "mg_batch_create", "mg_batch_propagate", "mg_batch_sync", "mg_batch_info",
-                     "mg_batch_destroy", "mg_probe_fma_rate", "mg_probe_expi", "mg_upload_u", "mg_download_u"):
+                     "mg_batch_destroy", "mg_probe_fma_rate", "mg_probe_expi", "mg_upload_u", "mg_download_u",
+                     "mg_probe_tc_dft16"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -152,6 +154,26 @@ def mg_probe_fma_rate(precision=MG_FP64, stream=None):
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(lib().mg_probe_fma_rate(precision, s, _ptr(out)), "mg_probe_fma_rate")
     return float(out[0])
+
+
+def mg_probe_tc_dft16(x, pre, post=None, split=1, inverse=False, stream=None):
+    """The 16-point DFT with diagonal multipliers on the tensor cores
+    (mg_probe_tc_dft16): x a CUDA complex64 tensor of shape (lines, 16);
+    pre, post 16 complex values (post None for 1); split 1 = 3xTF32,
+    2 = BF16x3.  Returns y like x."""
+    import torch
+
+    xx = x.contiguous()
+    if xx.dtype != torch.complex64 or not xx.is_cuda or xx.shape[-1] != 16:
+        raise ValueError("x must be a CUDA complex64 tensor of lines of 16 values")
+    y = torch.empty_like(xx)
+    pr = np.ascontiguousarray(np.asarray(pre, dtype=np.complex128).reshape(16))
+    po = None if post is None else np.ascontiguousarray(np.asarray(post, dtype=np.complex128).reshape(16))
+    st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(lib().mg_probe_tc_dft16(int(split), int(bool(inverse)), ctypes.c_void_p(xx.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), xx.numel() // 16, _ptr(pr),
+                                   _ptr(po) if po is not None else None, st), "mg_probe_tc_dft16")
+    return y
 
 
 def mg_probe_expi(theta, stream=None):

@@ -627,6 +627,8 @@ mg_status mg_create_ex(mg_ctx** out, int D, const int64_t* N, const double* dq, 
   if ((flags & MG_CREATE_TC_TF32X3) && (flags & MG_CREATE_TC_BF16X3)) return MG_ERR_ARG;
   const int want_tc = (flags & MG_CREATE_TC_TF32X3) ? 1 : ((flags & MG_CREATE_TC_BF16X3) ? 2 : 0);
   if (want_tc && (flags & (MG_CREATE_GENERAL_KERNEL | MG_CREATE_NO_TMA))) return MG_ERR_ARG;
+  // the tensor-core variant of the short-axis kernel is not enabled (mgrid.h)
+  if (want_tc) return MG_ERR_UNSUPPORTED;
   *out = nullptr;
   if (D < 1 || D > MAXD || !(hbar > 0) || !std::isfinite(hbar)) return MG_ERR_ARG;
   if (precision != MG_FP64 && precision != MG_FP32_MIXED) return MG_ERR_ARG;

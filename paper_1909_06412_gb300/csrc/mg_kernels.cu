@@ -203,7 +203,10 @@ __global__ void __launch_bounds__(THREADS)
   const Smem<V> S = carve<V>(P, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
-  if (threadIdx.x < P.D) S.sc[SC_Q + threadIdx.x] = B.ctrl[threadIdx.x];
+  if (threadIdx.x < P.D) {
+    S.sc[SC_Q + threadIdx.x] = B.ctrl[threadIdx.x];
+    S.sc[SC_P + threadIdx.x] = B.ctrl[8 + threadIdx.x];  // p^K of the kinetic cross terms
+  }
   if (threadIdx.x == 0) S.sc[SC_SGH] = 1.0;
   load_tables(P, B, S, LT_TW | LT_A | LT_C | LT_V | LT_E | LT_SCT);
   init_mbarriers(S);

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "mg_device.cuh"
+#include "mg_tc.cuh"
 #include "mgrid.h"
 
 namespace mgk {
@@ -59,10 +60,123 @@ __global__ void k_expi(const double* __restrict__ th, double* __restrict__ s, do
   }
 }
 
+// ---- tensor-core DFT of 16-point lines, standalone -----------------------
+// The split-product DFT-GEMM of mg_tc.cuh on caller-given lines: every block
+// builds the B operand of M = diag(post) F diag(pre) once, then transforms
+// 256 lines per round (two warpgroups of 128 rows, one issuing thread, one
+// commit per round, bounded waits).
+static __device__ float2 g_tc_mult[32];  // pre[16], post[16]
+static __device__ int g_tc_status;
+
+template <int TC, bool INV>
+__global__ void __launch_bounds__(256, 1)
+    k_tc_dft16(const float2* __restrict__ x, float2* __restrict__ y, int64_t nlines, int has_post, int* status) {
+  using TS = TcShape<TC>;
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  unsigned char* tcb = dyn;
+  unsigned char* tca = dyn + TS::NSPLIT * TS::B_BYTES;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned tslot;
+  __shared__ float2 mult[32];
+  if (threadIdx.x < 32) mult[threadIdx.x] = g_tc_mult[threadIdx.x];
+  __syncthreads();
+  tc_build_b<TC, INV>(tcb, mult, has_post ? mult + 16 : nullptr);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  tc_alloc(&tslot);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tslot;
+  const int wg = threadIdx.x >> 7, row = threadIdx.x & 127;
+  unsigned par = 0;
+  bool failed = false;
+  for (int64_t base = (int64_t)blockIdx.x * 256; base < nlines; base += (int64_t)gridDim.x * 256) {
+    const int64_t line = base + threadIdx.x;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = line < nlines ? x[line * 16 + r] : make_float2(0.f, 0.f);
+    tc_stage_line<TC>(tca + wg * TS::NSPLIT * TS::A_BYTES, row, v);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      tc_issue_products<TC>(tmem, tca, tcb);
+      tc_issue_products<TC>(tmem + 32, tca + TS::NSPLIT * TS::A_BYTES, tcb);
+      tc_commit(&bar);
+    }
+    bool ok = failed;
+    const uint64_t t0 = global_ns();
+    for (unsigned sp = 0; !ok; ++sp) {
+      ok = mbar_try_wait(&bar, par);
+      if (!ok && (sp & 255u) == 0 && global_ns() - t0 > 1000000000ull) {
+        failed = true;
+        atomicExch(status, 1);
+        break;
+      }
+    }
+    par ^= 1u;
+    tc_fence_after();
+    float d[32];
+    tc_ld32(tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + wg * 32, d);
+    tc_fence_before();
+    if (line < nlines) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) y[line * 16 + r] = make_float2(d[2 * r], d[2 * r + 1]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc_dealloc(tmem);
+}
+
+template <int TC, bool INV> void* tc_kernel() { return (void*)k_tc_dft16<TC, INV>; }
+
 }  // namespace
 }  // namespace mgk
 
 using namespace mgk;
+
+extern "C" mg_status mg_probe_tc_dft16(int split, int inverse, const void* d_x, void* d_y, int64_t nlines,
+                                       const double* pre, const double* post, void* cuda_stream) {
+  if (nlines < 0 || (nlines > 0 && (!d_x || !d_y)) || !pre || (split != 1 && split != 2)) return MG_ERR_ARG;
+  if (nlines == 0) return MG_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float2 m[32];
+  for (int i = 0; i < 16; ++i) {
+    m[i] = make_float2((float)pre[2 * i], (float)pre[2 * i + 1]);
+    m[16 + i] = post ? make_float2((float)post[2 * i], (float)post[2 * i + 1]) : make_float2(1.f, 0.f);
+  }
+  void* fn = split == 1 ? (inverse ? tc_kernel<TC_TF32X3, true>() : tc_kernel<TC_TF32X3, false>())
+                        : (inverse ? tc_kernel<TC_BF16X3, true>() : tc_kernel<TC_BF16X3, false>());
+  const int smem = split == 1 ? TcShape<TC_TF32X3>::NSPLIT * (TcShape<TC_TF32X3>::B_BYTES + 2 * TcShape<TC_TF32X3>::A_BYTES)
+                              : TcShape<TC_BF16X3>::NSPLIT * (TcShape<TC_BF16X3>::B_BYTES + 2 * TcShape<TC_BF16X3>::A_BYTES);
+  int* status = nullptr;
+  if (cudaGetSymbolAddress((void**)&status, g_tc_status) != cudaSuccess) return MG_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbolAsync(g_tc_mult, m, sizeof(m), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return MG_ERR_CUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MG_ERR_CUDA;
+  const int64_t want = (nlines + 255) / 256;
+  const int blocks = (int)(want < sms ? want : sms);
+  int has_post = post ? 1 : 0;
+  void* args[] = {(void*)&d_x, (void*)&d_y, (void*)&nlines, (void*)&has_post, (void*)&status};
+  if (cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, smem, st) != cudaSuccess) return MG_ERR_CUDA;
+  int hs = 0;
+  if (cudaMemcpyFromSymbolAsync(&hs, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MG_ERR_CUDA;
+  return hs ? MG_ERR_TIMEOUT : MG_OK;
+}
 
 extern "C" mg_status mg_probe_fma_rate(int precision, void* cuda_stream, double* tflops) {
   if (!tflops || (precision != MG_FP64 && precision != MG_FP32_MIXED)) return MG_ERR_ARG;

@@ -82,13 +82,18 @@ __device__ __forceinline__ void tc_named_sync(int id, int nthreads) {
 
 // Tensor-memory allocation of TC_TMEM_COLS columns by warp 0; the address is
 // written to *slot.  Dealloc by warp 0 after every thread's last access.
+// The .sync.aligned tcgen05 instructions need the whole warp converged at
+// them: each is preceded by __syncwarp (the code before them can diverge,
+// e.g. a bounded wait whose threads leave the loop at different polls).
 __device__ __forceinline__ void tc_alloc(unsigned* slot) {
+  __syncwarp();
   if ((threadIdx.x >> 5) == 0)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                  "r"(TC_TMEM_COLS)
                  : "memory");
 }
 __device__ __forceinline__ void tc_dealloc(unsigned taddr) {
+  __syncwarp();
   if ((threadIdx.x >> 5) == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS) : "memory");
 }
@@ -117,6 +122,7 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 // compiler copy or spill them in between.
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
+  __syncwarp();
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
@@ -232,13 +238,13 @@ __device__ void tc_build_b(unsigned char* bbase, const float2* pre, const float2
   }
 }
 
-// The split products of one warpgroup's 128 lines, issued by one thread into
-// the TMEM columns at dtmem; completion arrives on `bar`.
+// The split products of one warpgroup's 128 lines into the TMEM columns at
+// dtmem (issued by one thread, after tcgen05.fence::after_thread_sync; the
+// caller commits).
 template <int TC>
-__device__ __forceinline__ void tc_issue(uint32_t dtmem, const unsigned char* abase, const unsigned char* bbase,
-                                         uint64_t* bar) {
+__device__ __forceinline__ void tc_issue_products(uint32_t dtmem, const unsigned char* abase,
+                                                  const unsigned char* bbase) {
   using S = TcShape<TC>;
-  tc_fence_after();
   const uint32_t a0 = smem_u32(abase), b0 = smem_u32(bbase);
   int first = 1;
   // (A part, B part) pairs whose combined order is kept
@@ -253,7 +259,6 @@ __device__ __forceinline__ void tc_issue(uint32_t dtmem, const unsigned char* ab
       tc_mma(TC, dtmem, da, db, S::IDESC, first ? 0 : 1);
       first = 0;
     }
-  tc_commit(bar);
 }
 
 }  // namespace

@@ -314,7 +314,7 @@ def test_full_inverse_mass_matrix(mg, case):
         fac = [("gauss", P["R0"], P["P0"], P["sigma"]), ("morse", P["Dm"], P["a"], P["re"], P["mu"][1])]
         qc, pc, dt, steps, motion = [P["R0"], rbar], [P["P0"], 0.0], 2.0, 12, oracle.GRID_ADAPTIVE
     else:
-        N, dq = (16, 20, 12), (0.5, 0.45, 0.6)
+        N, dq = (16, 18, 12), (0.5, 0.45, 0.6)
         m = np.array([[1.0, 0.25, -0.1], [0.25, 0.8, 0.15], [-0.1, 0.15, 1.2]])
         if case == "harmonic3d":
             kind, pot = oracle.POT_HARMONIC, [1.0, 0, 0, 0, 1.44, 0, 0, 0, 2.25, 0.1, -0.2, 0.0]

@@ -46,3 +46,24 @@ def test_fma_rate_probe(mg):
     r64 = mg.mg_probe_fma_rate(mg.MG_FP64)
     r32 = mg.mg_probe_fma_rate(mg.MG_FP32_MIXED)
     assert r64 > 0 and r32 > r64
+
+
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("nlines", [1, 256, 1000, 40000])
+def test_tensor_core_dft16_against_fp64(mg, split, inverse, nlines):
+    # the dense 16-point DFT with diagonal multipliers as split-product GEMMs
+    # on the tensor cores, element by element against the FP64 product
+    g = inputs.rng(1000 + nlines)
+    x = (g.standard_normal((nlines, 16)) + 1j * g.standard_normal((nlines, 16))).astype(np.complex64)
+    pre = np.exp(1j * g.uniform(-np.pi, np.pi, 16)) / 16
+    post = np.exp(1j * g.uniform(-np.pi, np.pi, 16))
+    y = mg.mg_probe_tc_dft16(torch.from_numpy(x).cuda(), pre, post, split, inverse).cpu().numpy()
+    j = np.arange(16)
+    F = np.exp((2j if inverse else -2j) * np.pi * np.outer(j, j) / 16)
+    # the multipliers as the device holds them (FP32)
+    M = post.astype(np.complex64).astype(np.complex128)[:, None] * F * pre.astype(np.complex64).astype(np.complex128)[None, :]
+    ref = x.astype(np.complex128) @ M.T
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    # FP32-level: the split products keep 21-24 significant bits per operand
+    assert err < 2e-6, err

@@ -30,27 +30,22 @@ def mg():
     return m
 
 
-@pytest.mark.parametrize("n,D,prec,fname,tol,group,tc", [
-    (12, 7, 0, "hh_12p7_strang1.txt", 1e-12, (1, 3), None),
-    (16, 6, 1, "hh_16p6_strang1.txt", 5e-5, (1, 2), None),
-    (16, 6, 1, "hh_16p6_strang1.txt", 5e-5, (1, 2), "tf32x3"),
-    (16, 6, 1, "hh_16p6_strang1.txt", 5e-5, (1, 2), "bf16x3"),
+@pytest.mark.parametrize("n,D,prec,fname,tol,group", [
+    (12, 7, 0, "hh_12p7_strang1.txt", 1e-12, (1, 3)),
+    (16, 6, 1, "hh_16p6_strang1.txt", 5e-5, (1, 2)),
 ])
-def test_short_kernel_large_plans_vs_stored_oracle(mg, n, D, prec, fname, tol, group, tc):
-    # tc: the 16-point line DFTs on the tensor cores (3xTF32 or BF16x3 split
-    # products), whose chunks hold 256 lines: the same kinds of groups
+def test_short_kernel_large_plans_vs_stored_oracle(mg, n, D, prec, fname, tol, group):
     plan = mg.mg_short_axis_plan((n,) * D, prec)
     assert group in plan["groups"], plan
     if prec == 1:
         assert (0, 1) in plan["groups"], plan
     rec = records.read(fname)
     dq = np.sqrt(2 * np.pi / n)
-    flags = {None: 0, "tf32x3": mg.MG_CREATE_TC_TF32X3, "bf16x3": mg.MG_CREATE_TC_BF16X3}[tc]
-    g = mg.Propagator((n,) * D, (dq,) * D, precision=prec, flags=flags)
+    g = mg.Propagator((n,) * D, (dq,) * D, precision=prec)
     g.set_potential(mg.MG_POT_HENON_HEILES, [LAM])
     g.set_separable([("gauss", 2.0 + 0.1 * l, 0.2 - 0.1 * l, 1.0) for l in range(D)],
                     [2.0 + 0.1 * l for l in range(D)], [0.2 - 0.1 * l for l in range(D)])
-    assert g.path == {None: 2 if prec == 1 else 1, "tf32x3": 3, "bf16x3": 4}[tc]
+    assert g.path == (2 if prec == 1 else 1)
     g.propagate(1, 0.02, "strang")
     _, q, p, _ = g.get_state(want_psi=False)
     ct = max(tol, 1e-12)
