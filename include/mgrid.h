@@ -11,7 +11,7 @@
  * Substeps are composed symmetrically (eq:SO_TVT, eq:comp_TVT).
  *
  * Conventions shared by every entry point:
- *  - Grid: axis l has N_l points (even, 2 <= N_l <= 1024, only factors 2 and 3),
+ *  - Grid: axis l has N_l points (even, 2 <= N_l <= 2048, only factors 2 and 3),
  *    spacing dq_l > 0 and momentum spacing dp_l = 2 pi hbar / (N_l dq_l);
  *    x_l^J = q_l + (j_l - N_l/2) dq_l and p_l^K = p_l + (k_l - N_l/2) dp_l.
  *  - Arrays: row-major, last axis contiguous; complex values interleaved
@@ -223,6 +223,15 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
  * potential yet.  The same method either way (Sec. II.G); only the memory
  * traffic differs.  mg_create_ex's flags choose. */
 int mg_propagate_path(const mg_ctx* ctx);
+
+/* Where the general kernel reads its per-axis tables (Sec. II.G: the
+ * separable multipliers and potential columns, sum of N_l entries each):
+ * 0 = all in shared memory; bit 1 = the potential columns, k - N_l/2 and the
+ * kinetic energies stay in the workspace; bit 2 = the multipliers A, conj(A)/N
+ * and K too (FP64 only).  Chosen by mg_create when the tables and the data
+ * regions do not fit one CTA's shared memory (axis lengths summing to about
+ * 2000 or more).  -1 for a NULL context.  Host-only. */
+int mg_tables_in_workspace(const mg_ctx* ctx);
 
 /* Host-only (no GPU): the stage coefficients gamma_1..gamma_S of a named
  * composition (eq:comp_TVT), each stage a second-order step of length

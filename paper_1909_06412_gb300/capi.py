@@ -64,6 +64,8 @@ def lib():
         L.mg_kernel_launches.restype = i64
         L.mg_propagate_path.argtypes = [vp]
         L.mg_propagate_path.restype = i32
+        L.mg_tables_in_workspace.argtypes = [vp]
+        L.mg_tables_in_workspace.restype = i32
         L.mg_short_axis_plan.argtypes = [i32, vp, i32, vp, vp, vp, vp]
         L.mg_short_axis_plan.restype = i32
         L.mg_scheme_coefficients.argtypes = [ctypes.c_char_p, vp, i32]
@@ -351,8 +353,14 @@ class Propagator:
     @property
     def path(self):
         """Kernel of mg_propagate: 0 general, 1 short-axis, 2 short-axis with TMA
-        copies, 3 / 4 the same with tensor-core line DFTs (3xTF32 / BF16x3)."""
+        copies."""
         return int(lib().mg_propagate_path(self._h))
+
+    @property
+    def tables_in_workspace(self):
+        """mg_tables_in_workspace: which per-axis tables the general kernel
+        reads from the workspace instead of shared memory (bits 1 and 2)."""
+        return int(lib().mg_tables_in_workspace(self._h))
 
 
 def mg_batch_workspace_bytes(nprob):

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   using V = double2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sflag;
-  const Smem<V> S = carve<V>(P, smem_raw);
+  const Smem<V> S = carve<V>(P, B, smem_raw);
   // two more data regions for ubar, after the forward layout
   double2* breg[2];
   {

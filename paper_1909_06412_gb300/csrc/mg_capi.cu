@@ -124,7 +124,9 @@ size_t smem_for(const Plan& P) {
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
   const size_t TT = (size_t)P.tab_total;
-  size_t s = 4 * r16(vs * TT) + r16(sizeof(double) * NVCOL * TT) + 2 * r16(sizeof(double) * TT) +
+  const int nmult = (P.tab_global & TG_MULT) ? 0 : 3;
+  const int ncols = (P.tab_global & TG_COLS) ? 0 : 1;
+  size_t s = (1 + nmult) * r16(vs * TT) + ncols * (r16(sizeof(double) * NVCOL * TT) + 2 * r16(sizeof(double) * TT)) +
              r16(sizeof(double2) * 256) + r16(sizeof(double) * THREADS * (3 * P.D + 5)) +
              r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) +
              (P.resident ? 2 : 3) * r16((size_t)P.region_bytes) + r16(sizeof(uint64_t) * 3) +
@@ -163,7 +165,7 @@ void chunk_plan(Plan& P, int64_t region) {
   P.smem_bytes = (int)smem_for(P);
 }
 
-void tile_plan(Plan& P) {
+void tile_plan_tables(Plan& P) {
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const int D = P.D;
   int64_t need_res = 0, need_min = 0;
@@ -209,6 +211,21 @@ void tile_plan(Plan& P) {
     if (P.smem_bytes <= SMEM_CAP || region <= 4096) break;
     region = region - region / 8 - 16;
   }
+}
+
+// Tiles and chunks, with the per-axis tables in shared memory when they fit
+// beside the data regions; long axes (sum of lengths in the thousands) keep
+// their potential columns, and for FP64 their multipliers too, in the
+// workspace.
+void tile_plan(Plan& P) {
+  P.tab_global = 0;
+  tile_plan_tables(P);
+  if (P.smem_bytes <= SMEM_CAP) return;
+  P.tab_global = TG_COLS;
+  tile_plan_tables(P);
+  if (P.smem_bytes <= SMEM_CAP || P.prec != 0) return;
+  P.tab_global = TG_COLS | TG_MULT;
+  tile_plan_tables(P);
 }
 
 // Shared memory of the short-axis kernel for regions of `re` elements: sets
@@ -1288,9 +1305,10 @@ int64_t mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : -1; }
 int mg_propagate_path(const mg_ctx* c) {
   if (!c || !c->pot_set) return -1;
   if (!c->SP.on || !uses_short_kernel(c->P)) return 0;
-  if (c->SP.tc) return 2 + c->SP.tc;
   return c->SP.tma ? 2 : 1;
 }
+
+int mg_tables_in_workspace(const mg_ctx* c) { return c ? c->P.tab_global : -1; }
 
 int mg_scheme_coefficients(const char* scheme, double* gamma, int max) {
   std::vector<double> g;
@@ -1778,6 +1796,7 @@ mg_status mg_batch_create(mg_batch** out, int nprob, mg_ctx* const* ctxs, int cl
     for (int i = 0; i < nprob; ++i) {
       Plan& P = b->hprob[i].P;
       P = ctxs[i]->P;
+      P.tab_global = 0;  // the batched kernel keeps every table in shared memory
       const int64_t t = (tile_bytes && tile_bytes[i] ? tile_bytes[i] : def_target) * scale_num / scale_den;
       big = std::max(big, batch_tiles(P, cluster, std::max<int64_t>(t, 1)));
       A.D = std::max(A.D, P.D);

@@ -348,7 +348,7 @@ template <typename V> struct Smem {
   size_t end;   // bytes used
 };
 
-template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* base) {
+template <typename V> __device__ Smem<V> carve(const Plan& P, const Bufs& B, unsigned char* base) {
   Smem<V> s;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -358,12 +358,25 @@ template <typename V> __device__ Smem<V> carve(const Plan& P, unsigned char* bas
   };
   const int TT = P.tab_total;
   s.tw = (V*)take(sizeof(V) * TT);
-  s.tA = (V*)take(sizeof(V) * TT);
-  s.tAi = (V*)take(sizeof(V) * TT);
-  s.tK = (V*)take(sizeof(V) * TT);
-  s.tv = (double*)take(sizeof(double) * NVCOL * TT);
-  s.tc = (double*)take(sizeof(double) * TT);
-  s.te = (double*)take(sizeof(double) * TT);
+  if (P.tab_global & TG_MULT) {
+    // FP64 only (V = double2): the workspace tables themselves
+    s.tA = (V*)B.tabA;
+    s.tAi = (V*)B.tabAi;
+    s.tK = (V*)B.tabK;
+  } else {
+    s.tA = (V*)take(sizeof(V) * TT);
+    s.tAi = (V*)take(sizeof(V) * TT);
+    s.tK = (V*)take(sizeof(V) * TT);
+  }
+  if (P.tab_global & TG_COLS) {
+    s.tv = B.tabV;
+    s.tc = B.tabC;
+    s.te = B.tabE;
+  } else {
+    s.tv = (double*)take(sizeof(double) * NVCOL * TT);
+    s.tc = (double*)take(sizeof(double) * TT);
+    s.te = (double*)take(sizeof(double) * TT);
+  }
   s.sct = (double2*)take(sizeof(double2) * 256);
   s.red = (double*)take(sizeof(double) * THREADS * (3 * P.D + 5));
   s.fin = (double*)take(sizeof(double) * PSTRIDE);
@@ -384,6 +397,10 @@ enum { LT_TW = 1, LT_A = 2, LT_K = 4, LT_V = 8, LT_C = 16, LT_E = 32, LT_SCT = 6
 // Copy tables from global memory (written by other CTAs) into shared memory.
 template <typename V> __device__ void load_tables(const Plan& P, const Bufs& B, const Smem<V>& S, int what) {
   const int TT = P.tab_total;
+  // tables kept in the workspace are read there (after the grid barrier that
+  // follows their build, like every other global value)
+  if (P.tab_global & TG_MULT) what &= ~(LT_A | LT_K);
+  if (P.tab_global & TG_COLS) what &= ~(LT_V | LT_C | LT_E);
   // every load of an entry is issued before its shared-memory stores, so that
   // the L2 round trips of an entry overlap instead of following one another
   for (int e = threadIdx.x; e < TT; e += blockDim.x) {

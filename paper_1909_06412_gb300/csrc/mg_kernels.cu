@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   using V = typename VT<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sflag;
-  const Smem<V> S = carve<V>(P, smem_raw);
+  const Smem<V> S = carve<V>(P, B, smem_raw);
   const int D = P.D;
   // an unreported error from an earlier launch makes every later launch a no-op
   if (__ldcg(B.status) != ST_OK) return;
@@ -165,7 +165,7 @@ template <typename T>
 __global__ void __launch_bounds__(THREADS) k_init_tables(const __grid_constant__ Plan P,
                                                           const __grid_constant__ Bufs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, smem_raw);
+  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, B, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x < P.D) {
@@ -182,7 +182,7 @@ template <typename T>
 __global__ void __launch_bounds__(THREADS) k_obs_tables(const __grid_constant__ Plan P,
                                                          const __grid_constant__ Bufs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, smem_raw);
+  const Smem<typename VT<T>::v> S = carve<typename VT<T>::v>(P, B, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x < P.D) {
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(THREADS)
     k_obs_pass(const __grid_constant__ Plan P, const __grid_constant__ Bufs B, int l, int mode) {
   using V = typename VT<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<V> S = carve<V>(P, smem_raw);
+  const Smem<V> S = carve<V>(P, B, smem_raw);
   if (threadIdx.x < SC_N) S.sc[threadIdx.x] = 0.0;
   __syncthreads();
   if (threadIdx.x < P.D) {

@@ -8,7 +8,7 @@ namespace mgk {
 
 constexpr int MAXD = 8;        // axes
 constexpr int MAXRAD = 12;     // Stockham passes per axis
-constexpr int MAXN = 1024;     // longest axis
+constexpr int MAXN = 2048;     // longest axis
 constexpr int PSTRIDE = 16;    // doubles per CTA partial-sum record
 constexpr int NVCOL = 5;       // potential-table columns per axis
 constexpr int MAX_STAGES = 625;
@@ -19,6 +19,10 @@ constexpr int CTRL = 64;       // doubles of the control block in the workspace
 enum { POT_HARMONIC = 0, POT_ATOM_DIATOM = 1, POT_HENON_HEILES = 2, POT_SECREST_JOHNSON = 3 };
 enum { SPLIT_TVT = 0, SPLIT_VTV = 1, SPLIT_TV = 2 };
 enum { GRID_ADAPTIVE = 0, GRID_CENTRE_P = 1, GRID_FIXED = 2 };
+// Per-axis tables too large for shared memory (long axes) stay in the workspace:
+// TG_COLS the potential columns, k - N/2 and the kinetic energies; TG_MULT
+// (FP64 only) the multipliers A, conj(A)/N and K.
+enum { TG_COLS = 1, TG_MULT = 2 };
 enum { ST_OK = 0, ST_TIMEOUT = -4, ST_NONFINITE = -5, ST_UNSTABLE = -6 };
 
 // One axis of the tensor-product grid and how its 1D transforms are tiled.
@@ -45,6 +49,7 @@ struct Plan {
   int smem_bytes;        // dynamic smem per CTA
   int max_tiles;         // most tiles in one smem chunk (any axis)
   int max_lines;         // most lines in one smem chunk (any axis)
+  int tab_global;        // TG_* bits: per-axis tables read from the workspace, not shared memory
   int64_t npts;
   int64_t N[MAXD];
   double dq[MAXD], dp[MAXD], minv[MAXD], hbar;  // minv: diagonal of the inverse mass matrix

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   using V = typename VT<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sflag;
-  const Smem<V> S = carve<V>(P, smem_raw);
+  const Smem<V> S = carve<V>(P, B, smem_raw);
   const int D = P.D;
   if (__ldcg(B.status) != ST_OK) return;
   double* sc = S.sc;

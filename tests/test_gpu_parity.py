@@ -128,7 +128,7 @@ def test_splits_and_grid_motion(mg, split, motion):
 # other potentials, axis lengths and dimensions (ragged, radix 3, D=1..8)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N", [(2,), (6,), (12,), (64,), (96,), (1024,)])
+@pytest.mark.parametrize("N", [(2,), (6,), (12,), (64,), (96,), (1024,), (2048,)])
 def test_one_dimension(mg, N):
     dq = (8.0 / N[0],) if N[0] > 6 else (0.9,)
     g, o = pair(mg, N, dq, (0.8,), oracle.POT_HARMONIC, [1.7, 0.3])
@@ -186,6 +186,28 @@ def test_secrest_johnson_vtv(mg):
     g.propagate(30, 0.1, "yoshida4", oracle.SPLIT_VTV)
     o.propagate(30, 0.1, "yoshida4", oracle.SPLIT_VTV)
     assert_same(g, o)
+
+
+@pytest.mark.parametrize("N,motion,bits", [
+    ((128, 2048), oracle.GRID_FIXED, 3),
+    ((128, 2048), oracle.GRID_ADAPTIVE, 3),
+    ((64, 1536), oracle.GRID_ADAPTIVE, 1),
+])
+def test_long_axis_tables_in_workspace(mg, N, motion, bits):
+    # Sec. III.B's Secrest-Johnson model on grids whose per-axis tables do not
+    # fit shared memory beside the data regions: the general kernel reads them
+    # from the workspace (the 128 x 2048 fixed reference grid of the paper)
+    rng1, rng2 = 28.0, 96.0
+    dq = (rng1 / N[0], rng2 / N[1])
+    g, o = pair(mg, N, dq, (1.0, 1.5), oracle.POT_SECREST_JOHNSON, [20.0, 0.158, 0.3])
+    assert g.tables_in_workspace == bits
+    fac = [("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.56, np.sqrt(8.0))]
+    g.set_separable(fac, [0.0, 24.0], [0.0, -3.56])
+    o.set_separable(fac, [0.0, 24.0], [0.0, -3.56])
+    g.propagate(6, 0.1, "yoshida4", oracle.SPLIT_VTV, motion)
+    o.propagate(6, 0.1, "yoshida4", oracle.SPLIT_VTV, motion)
+    assert_same(g, o)
+    assert abs(g.observables()[1] - o.observables()[1]) < 1e-11 * abs(o.observables()[1])
 
 
 def test_random_state_and_centre(mg):
