@@ -46,6 +46,7 @@ CPU_SAMPLE_STEPS = 30
 # headline: 8D Henon-Heiles, 12^8 FP64
 HH_N, HH_D, HH_LAM = 12, 8, 0.111803
 HH_SCHEME, HH_STAGES, HH_DT = "suzuki4", 5, 0.01
+HH_STEPS_PER_CALL = 4  # time steps per timed call: 4 x 5 stages, 21 kinetic units after merging
 HH_E2E_ITERS = 5
 HH_CPU_D = 5   # oracle sample: the same model on 12^5, one time step
 HH_REF_D = 4   # reference arm: one time step on 12^4 per timed step
@@ -191,7 +192,7 @@ def headline_config(world):
                     f"({HH_N ** HH_D:.3g} points, {16 * HH_N ** HH_D / 1e9:.2f} GB), {HH_SCHEME} "
                     f"({HH_STAGES} TVT stages per step), dt = {HH_DT}, lambda = {HH_LAM}",
         "grid": [HH_N] * HH_D, "scheme": HH_SCHEME, "stages_per_step": HH_STAGES, "dt": HH_DT,
-        "time_steps_per_iteration": 1,
+        "time_steps_per_iteration": HH_STEPS_PER_CALL,
         "parallelism": "replicas" if world > 1 else "single GPU",
     }
 
@@ -256,8 +257,9 @@ def cpu_model():
 
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (one thread) for the headline
-    model: each timed step is one time step on a 12^4 grid (a bounded sample
-    of the 12^8 workload: same model, axis length, scheme and dt)."""
+    model: each timed step is HH_STEPS_PER_CALL time steps on a 12^4 grid (a
+    bounded sample of the 12^8 workload: same model, axis length, scheme, dt
+    and steps per iteration)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -268,11 +270,11 @@ def run_reference(args):
         o.propagate(1, HH_DT, HH_SCHEME)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.propagate(1, HH_DT, HH_SCHEME)
+        o.propagate(HH_STEPS_PER_CALL, HH_DT, HH_SCHEME)
     el = time.perf_counter() - t0
     npts = HH_N ** HH_REF_D
-    v = npts * args.steps / el
-    sample = (f"{args.steps} time steps of the headline model on a {HH_N}^{HH_REF_D} grid (the oracle's cost "
+    v = npts * HH_STEPS_PER_CALL * args.steps / el
+    sample = (f"{args.steps} x {HH_STEPS_PER_CALL} time steps of the headline model on a {HH_N}^{HH_REF_D} grid (the oracle's cost "
               f"per point grows with the number of axes, so this favours it), single thread, {cpu_model()}")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -329,13 +331,25 @@ def hh_propagator(mgmod, n, D, prec, dev=None):
 def run_profile(args):
     """The timed launches of a workload alone, for profiler captures: the
     propagate kernel is launched warmup + steps times.  --profile-case
-    hh8_fp64 (default): the headline, 12^8 FP64, one time step per call;
+    hh8_fp64 (default): the headline, 12^8 FP64, HH_STEPS_PER_CALL time steps
+    per call as timed;
     hh7_fp64 / hh7_fp32: Henon-Heiles on 12^7 (FP64) / 16^7 (FP32) grids, the
     small cases for full captures; atom_diatom: the 256 x 256 workload,
-    STEPS_PER_CALL steps per call."""
+    STEPS_PER_CALL steps per call; tc_dft16: the standalone 16-point DFT on
+    TC_PROFILE_LINES lines, register form then 3xTF32 then BF16x3."""
     import torch
     import paper_1909_06412_gb300 as mg
 
+    if args.profile_case == "tc_dft16":
+        x, pre, post = dft16_inputs(torch, torch.device("cuda", 0), TC_PROFILE_LINES)
+        y = torch.empty_like(x)
+        st = torch.cuda.current_stream()
+        for split in (0, 1, 2):
+            for _ in range(args.warmup + args.steps):
+                mg.mg_probe_tc_dft16(x, pre, post, split, False, st, out=y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "case": args.profile_case, "lines": TC_PROFILE_LINES}))
+        return
     if args.profile_case == "atom_diatom":
         fac, qc, pc = initial(mg)
         g = mg.Propagator(N_GRID, DQ, minv=MINV)
@@ -346,7 +360,8 @@ def run_profile(args):
         n, D, prec = {"hh8_fp64": (12, 8, mg.MG_FP64), "hh7_fp32": (16, 7, mg.MG_FP32_MIXED),
                       "hh7_fp64": (12, 7, mg.MG_FP64)}[args.profile_case]
         g = hh_propagator(mg, n, D, prec)
-        call = lambda: g.propagate(1, 0.01, "suzuki4")
+        k = HH_STEPS_PER_CALL if args.profile_case == "hh8_fp64" else 1
+        call = lambda: g.propagate(k, HH_DT, HH_SCHEME)
     for _ in range(args.warmup + args.steps):
         call()
     g.sync()
@@ -622,19 +637,25 @@ def batch_problem_setup(mgmod, pr, precision):
     """One problem of the seeded batch workload as a Propagator."""
     g = mgmod.Propagator(pr["N"], pr["dq"], minv=1.0 / np.array(pr["mass"]), precision=precision)
     if pr["kind"] == "atom_diatom":
-        Dm, a, re, A, be = pr["pot"]
         g.set_potential(mgmod.MG_POT_ATOM_DIATOM, list(pr["pot"]))
+    else:
+        k, c = pr["pot"]
+        g.set_potential(mgmod.MG_POT_HARMONIC, list(np.diag(k).ravel()) + list(c))
+    batch_problem_initial(mgmod, g, pr)
+    return g
+
+
+def batch_problem_initial(mgmod, g, pr):
+    """(Re)set a batch problem's initial state and grid centre."""
+    if pr["kind"] == "atom_diatom":
+        Dm, a, re, A, be = pr["pot"]
         R0, P0, sg = pr["gauss"][0]
         mr = pr["mass"][1]
         g.set_separable([("gauss", R0, P0, sg), ("morse", Dm, a, re, mr)],
                         [R0, mgmod.mg_morse_mean(Dm, a, re, mr)], [P0, 0.0])
     else:
-        k, c = pr["pot"]
-        D = len(k)
-        g.set_potential(mgmod.MG_POT_HARMONIC, list(np.diag(k).ravel()) + list(c))
         g.set_separable([("gauss", q, p, sg) for q, p, sg in pr["gauss"]],
                         [f[0] for f in pr["gauss"]], [f[1] for f in pr["gauss"]])
-    return g
 
 
 def batch_leg(mgmod, torch, dev):
@@ -658,6 +679,7 @@ def batch_leg(mgmod, torch, dev):
     t0 = time.perf_counter()
     s, tb, rm, entry = autotune.tune_batch(gs, BATCH_STEPS, dts, "suzuki4", trial_steps=4, cache_path=cache)
     tune_s = time.perf_counter() - t0
+    MEASURED["batch_knobs_fp32"] = {"cluster": s["cluster"], "tile_bytes": tb, "radix_max": rm}
     out = {"workload": "seeded 512-grid batch (2D 64^2-256^2, 3D 16^3-48^3), FP32 storage + FP64 reductions, "
                        "suzuki4", "points": int(pts.sum()), "problems": len(probs),
            "autotune": {"settings": s, "trials": entry["trials"], "tuning_s": tune_s,
@@ -709,6 +731,325 @@ def batch_leg(mgmod, torch, dev):
         g.close()
     del gd
     torch.cuda.empty_cache()
+    return out
+
+
+TC_LINES = 1 << 22          # 64 M points: 512 MB in and 512 MB out, larger than L2
+TC_PROFILE_LINES = 1 << 21
+
+
+def dft16_inputs(torch, dev, nlines):
+    """Seeded lines of 16 complex64 values and unit-modulus multipliers (the
+    demodulation factor with the 1/16 of the transform pair, and a kinetic
+    phase)."""
+    g = np.random.default_rng(20190913)
+    gen = torch.Generator(device=dev).manual_seed(20190913)
+    x = torch.randn((nlines, 16), dtype=torch.complex64, device=dev, generator=gen)
+    pre = np.exp(1j * g.uniform(-np.pi, np.pi, 16)) / 16
+    post = np.exp(1j * g.uniform(-np.pi, np.pi, 16))
+    return x, pre, post
+
+
+def tc_dft16_leg(mgmod, torch, dev):
+    """The 16-point line DFT of the FP32 16^D grids (eq:F_defintion along one
+    axis, with its diagonal multipliers) as a standalone batched kernel in three
+    forms: FP32 registers (the short-axis kernel's codelet), and the dense
+    DFT-GEMM on the tensor cores (tcgen05.mma, kind::tf32 with 3xTF32 split
+    products; kind::f16 with BF16x3).  Each is timed with CUDA events over 5
+    launches on TC_LINES lines after 2 warm-up launches, and its error is taken
+    against the FP64 product on 4096 sampled lines."""
+    x, pre, post = dft16_inputs(torch, dev, TC_LINES)
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream(dev)
+    sample = torch.arange(0, TC_LINES, TC_LINES // 4096, device=dev)
+    xs = x[sample].cpu().numpy().astype(np.complex128)
+    j = np.arange(16)
+    F = np.exp(-2j * np.pi * np.outer(j, j) / 16)
+    M = post.astype(np.complex64).astype(np.complex128)[:, None] * F * \
+        pre.astype(np.complex64).astype(np.complex128)[None, :]
+    ref = xs @ M.T
+    npts = TC_LINES * 16
+    out = {"workload": f"{TC_LINES} lines of 16 complex64 points ({npts * 8 / 1e9:.2f} GB in and out), "
+                       "y = diag(post) F diag(pre) x", "bytes_per_point": 16,
+           "dense_flops_per_point": 128}
+    for split, name, mult in ((0, "register_fp32", 1), (1, "tcgen05_3xtf32", 3), (2, "tcgen05_bf16x3", 6)):
+        for _ in range(2):
+            mgmod.mg_probe_tc_dft16(x, pre, post, split, False, st, out=y)
+        ms = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            mgmod.mg_probe_tc_dft16(x, pre, post, split, False, st, out=y)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms) / 1e3
+        err = float(np.abs(y[sample].cpu().numpy() - ref).max() / np.abs(ref).max())
+        gbs = npts * 16 / t / 1e9
+        out[name] = {"ms": 1e3 * t, "points_per_s": npts / t, "hbm_gbs": gbs,
+                     "hbm_frac": gbs / peaks()[0],
+                     "tensor_tflops": None if split == 0 else npts * 128 * mult / t / 1e12,
+                     "max_rel_error_vs_fp64": err}
+    best = min(("register_fp32", "tcgen05_3xtf32", "tcgen05_bf16x3"), key=lambda k: out[k]["ms"])
+    out["fastest"] = best
+    del x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+# Sec. III.A: 3D harmonic model (Table I), adaptive 32^3 (dq 0.4375) against
+# the fixed 128^3 grid with twice the q and p ranges; t_f = 50, dt = t_f / 2^9.
+E2_TF, E2_STEPS, E2_CHECK = 50.0, 512, 128
+# Sec. III.B: He-H2 scattering (eq:modified_secrest_johnson), VTV, dt = 0.1:
+# adaptive and fixed 128 x 128 grids (q1 in (-14, 14), q2 in (0, 48)) against
+# the fixed 128 x 2048 reference (q2 in (-50, 400)).
+E7_DT, E7_STEPS, E7_CHECK = 0.1, 400, 50
+ACC_SCHEME = "yoshida10"  # the tenth-order triple jump stands in for the unprinted optimal scheme
+
+
+def adaptive_vs_fixed_leg(mgmod, torch, dev):
+    """The accuracy of grid adaptation as the paper measures it (Figs. 3 and
+    8): the distance ||psi_t - Psi_t|| between the adaptive-grid state and a
+    fixed-grid reference on a larger, denser grid, the sparser state carried
+    onto the denser grid by trigonometric interpolation (tests/grid_distance),
+    and the difference of <q>.  Both runs use the same composition and dt."""
+    from tests import grid_distance as gd
+    from tests import inputs
+
+    def grid_of(g):
+        _, q, p, _ = g.get_state(want_psi=False)
+        return {"N": list(g.N), "dq": list(g.dq), "q": list(q), "p": list(p)}
+
+    def harmonic(N, dq):
+        P = inputs.DUSCHINSKY3D
+        g = mgmod.Propagator(N, dq, minv=P["omega"], device=dev)
+        g.set_potential(mgmod.MG_POT_HARMONIC, list(np.array(P["K"]).ravel()) + list(P["q0"]))
+        g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 3, [0.0] * 3, [0.0] * 3)
+        return g
+
+    out = {"scheme": ACC_SCHEME}
+    # E2: 3D harmonic
+    dt = E2_TF / E2_STEPS
+    ga = harmonic((32,) * 3, (0.4375,) * 3)
+    gf = harmonic((128,) * 3, (0.21875,) * 3)
+    rows = []
+    t_a = t_f = 0.0
+    for k in range(E2_STEPS // E2_CHECK + 1):
+        if k:
+            for g, motion, acc in ((ga, mgmod.MG_GRID_ADAPTIVE, "a"), (gf, mgmod.MG_GRID_FIXED, "f")):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(g.stream)
+                g.propagate(E2_CHECK, dt, ACC_SCHEME, mgmod.MG_TVT, motion)
+                e1.record(g.stream)
+                g.sync()
+                if acc == "a":
+                    t_a += e0.elapsed_time(e1) / 1e3
+                else:
+                    t_f += e0.elapsed_time(e1) / 1e3
+        psi_a, psi_f = ga.get_state()[0], gf.get_state()[0]
+        sa, sf = grid_of(ga), grid_of(gf)
+        rows.append({"t": k * E2_CHECK * dt, "distance": gd.distance(psi_a, sa, psi_f, sf),
+                     "dq_mean_max": float(np.abs(gd.mean_q(psi_a, sa) - gd.mean_q(psi_f, sf)).max()),
+                     "grid_centre_q": sa["q"]})
+    out["E2_harmonic_3d"] = {
+        "workload": f"Sec. III.A model (Table I, K13 = +0.017): adaptive 32^3 (dq 0.4375) vs fixed 128^3 "
+                    f"(dq 0.21875), {ACC_SCHEME} TVT, dt = t_f/{E2_STEPS}, t_f = {E2_TF}",
+        "paper": "5e-11 at t = 0 and 2e-10 at t_f (optimal tenth-order scheme)",
+        "rows": rows, "gpu_s_adaptive": t_a, "gpu_s_fixed": t_f}
+    ga.close(); gf.close()
+    del ga, gf
+    torch.cuda.empty_cache()
+
+    # E7: He-H2 scattering
+    sj = [20.0, 0.158, 0.3]
+    fac = [("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.56, np.sqrt(8.0))]
+
+    def scattering(N, lo2, hi2):
+        dq = (28.0 / N[0], (hi2 - lo2) / N[1])
+        qc2 = lo2 + (N[1] // 2) * dq[1]
+        g = mgmod.Propagator(N, dq, minv=(1.0, 1.5), device=dev)
+        g.set_potential(mgmod.MG_POT_SECREST_JOHNSON, sj)
+        g.set_separable(fac, [0.0, qc2], [0.0, -3.56])
+        return g
+
+    runs = {"adaptive_128x128": (scattering((128, 128), 0.0, 48.0), mgmod.MG_GRID_ADAPTIVE),
+            "fixed_128x128": (scattering((128, 128), 0.0, 48.0), mgmod.MG_GRID_FIXED),
+            "reference_fixed_128x2048": (scattering((128, 2048), -50.0, 400.0), mgmod.MG_GRID_FIXED)}
+    ref = runs["reference_fixed_128x2048"][0]
+    rows = []
+    secs = {k: 0.0 for k in runs}
+    for k in range(E7_STEPS // E7_CHECK + 1):
+        if k:
+            for name, (g, motion) in runs.items():
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(g.stream)
+                g.propagate(E7_CHECK, E7_DT, ACC_SCHEME, mgmod.MG_VTV, motion)
+                e1.record(g.stream)
+                g.sync()
+                secs[name] += e0.elapsed_time(e1) / 1e3
+        psi_r, sr = ref.get_state()[0], grid_of(ref)
+        row = {"t": k * E7_CHECK * E7_DT}
+        for name in ("adaptive_128x128", "fixed_128x128"):
+            g = runs[name][0]
+            psi, s = g.get_state()[0], grid_of(g)
+            row[name] = {"distance": gd.distance(psi, s, psi_r, sr),
+                         "dq_mean": list(gd.mean_q(psi, s) - gd.mean_q(psi_r, sr))}
+        rows.append(row)
+    out["E7_scattering"] = {
+        "workload": f"Sec. III.B He-H2 (eq:modified_secrest_johnson), {ACC_SCHEME} VTV, dt = {E7_DT}: adaptive "
+                    f"and fixed 128 x 128 grids vs the fixed 128 x 2048 reference",
+        "paper": "adaptive error < 1e-3 six times longer than the fixed grid's; <q> error small until t ~ 20",
+        "rows": rows, "gpu_s": secs,
+        "reference_tables_in_workspace": ref.tables_in_workspace}
+    for g, _ in runs.values():
+        g.close()
+    del runs, ref
+    torch.cuda.empty_cache()
+    return out
+
+
+# Equal stated error: every (precision, scheme, dt) of the atom-diatom 256^2
+# workload run to EQ_T, its distance to an FP64 eighth-order run at dt 0.125,
+# and per target error the fastest run of each precision that meets it.
+EQ_T = 32.0
+EQ_DTS = (2.0, 1.0, 0.5, 0.25)
+EQ_SCHEMES = (("strang", 1), ("yoshida4", 3), ("suzuki4", 5), ("yoshida6", 9))
+EQ_TARGETS = (1e-3, 1e-4, 1e-5, 1e-6, 1e-8, 1e-10)
+
+
+def pick_fastest(runs, target):
+    ok = [r for r in runs if r["error"] <= target]
+    return min(ok, key=lambda r: r["s"]) if ok else None
+
+
+def equal_error_leg(mgmod, torch, dev):
+    """Mixed precision (FP32 storage and transforms) against plain FP64 at an
+    equal stated error on the atom-diatom 256 x 256 workload: the time to reach
+    t = EQ_T with an error below each target, choosing for each precision the
+    fastest composition and time step that meets it."""
+    from tests import grid_distance as gd
+
+    def grid_of(g):
+        _, q, p, _ = g.get_state(want_psi=False)
+        return {"N": list(g.N), "dq": list(g.dq), "q": list(q), "p": list(p)}
+
+    ref = headline_propagator(mgmod, dev)
+    ref.propagate(int(round(EQ_T / 0.125)), 0.125, "yoshida8")
+    psi_r, sr = ref.get_state()[0], grid_of(ref)
+    ref.close()
+    out = {"workload": f"collinear atom-diatom 256x256, t = {EQ_T} a.u.",
+           "reference": "FP64 yoshida8, dt = 0.125 a.u.",
+           "error_definition": "||psi - psi_ref||, psi carried onto the reference grid", "runs": []}
+    for prec, pname in ((mgmod.MG_FP64, "fp64"), (mgmod.MG_FP32_MIXED, "fp32_mixed")):
+        w = headline_propagator(mgmod, dev, prec)  # warm-up of this precision's kernels
+        w.propagate(4, 1.0, "yoshida6")
+        w.close()
+        for scheme, stages in EQ_SCHEMES:
+            for dt in EQ_DTS:
+                g = headline_propagator(mgmod, dev, prec)
+                n = int(round(EQ_T / dt))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(g.stream)
+                g.propagate(n, dt, scheme)
+                e1.record(g.stream)
+                g.sync()
+                psi = g.get_state()[0]
+                out["runs"].append({"precision": pname, "scheme": scheme, "dt": dt, "stages": n * stages,
+                                    "s": e0.elapsed_time(e1) / 1e3,
+                                    "error": gd.distance(psi, grid_of(g), psi_r, sr)})
+                g.close()
+    rows = []
+    for eps in EQ_TARGETS:
+        a = pick_fastest([r for r in out["runs"] if r["precision"] == "fp64"], eps)
+        b = pick_fastest([r for r in out["runs"] if r["precision"] == "fp32_mixed"], eps)
+        rows.append({"target_error": eps, "fp64": a, "fp32_mixed": b,
+                     "mixed_beats_fp64": None if a is None else (b is not None and b["s"] < a["s"]),
+                     "fp64_s_over_mixed_s": a["s"] / b["s"] if a and b else None})
+    out["at_equal_error"] = rows
+    torch.cuda.empty_cache()
+    return out
+
+
+BATCH_EQ_STEPS = 40
+BATCH_EQ_MULT = (1, 2, 4, 8)
+
+
+def batch_equal_error_leg(mgmod, torch, dev, knobs32):
+    """The batched launch at an equal stated error on the seeded 512-grid
+    workload: FP64 and FP32 batches run the same simulated time with the
+    problems' time steps multiplied by 1, 2, 4, 8 (BATCH_EQ_STEPS / k steps);
+    errors on every 64th problem against an FP64 single-grid yoshida8 run at
+    the base time step.  Also the FP64 batch against the 512 separate FP64
+    launches over the same step count."""
+    from paper_1909_06412_gb300 import autotune
+    import tempfile
+    from tests import inputs
+
+    probs = inputs.batch_problems()
+    dts = np.array([pr["dt"] for pr in probs])
+    pts = np.array([int(np.prod(pr["N"])) for pr in probs])
+    sample = list(range(0, len(probs), 64))
+    refs = []
+    for i in sample:
+        r = batch_problem_setup(mgmod, probs[i], mgmod.MG_FP64)
+        r.propagate(BATCH_EQ_STEPS, dts[i], "yoshida8")
+        refs.append(r.get_state()[0])
+        r.close()
+    out = {"workload": "seeded 512-grid batch, suzuki4", "simulated_steps_at_base_dt": BATCH_EQ_STEPS,
+           "reference": "FP64 single-grid yoshida8 at the base time step", "runs": []}
+    for prec, pname in ((mgmod.MG_FP64, "fp64"), (mgmod.MG_FP32_MIXED, "fp32_mixed")):
+        gs = [batch_problem_setup(mgmod, pr, prec) for pr in probs]
+        if prec == mgmod.MG_FP64:
+            cache = os.path.join(tempfile.mkdtemp(), "autotune64.json")
+            s, tb, rm, _ = autotune.tune_batch(gs, BATCH_EQ_STEPS, dts, "suzuki4", trial_steps=4, cache_path=cache)
+            knobs = {"cluster": s["cluster"], "tile_bytes": tb, "radix_max": rm}
+            for g, pr in zip(gs, probs):
+                batch_problem_initial(mgmod, g, pr)
+        else:
+            knobs = knobs32
+        for k in BATCH_EQ_MULT:
+            b = mgmod.Batch(gs, **knobs)
+            n = BATCH_EQ_STEPS // k
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(gs[0].stream)
+            b.propagate(n, dts * k, "suzuki4")
+            e1.record(gs[0].stream)
+            b.sync()
+            t = e0.elapsed_time(e1) / 1e3
+            err = max(float(np.linalg.norm(gs[i].get_state()[0] - ref) / np.linalg.norm(ref))
+                      for i, ref in zip(sample, refs))
+            out["runs"].append({"precision": pname, "dt_multiplier": k, "steps": n, "s": t, "error": err,
+                                "value": float(pts.sum()) * n / t, "unit": UNIT})
+            b.close()
+            for g, pr in zip(gs, probs):
+                batch_problem_initial(mgmod, g, pr)
+        if prec == mgmod.MG_FP64:
+            # the same problems as separate plain FP64 launches, same step count
+            for g, dt in zip(gs, dts):
+                g.propagate(1, dt, "suzuki4")
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(gs[0].stream)
+            for g, dt in zip(gs, dts):
+                g.propagate(BATCH_EQ_STEPS, dt, "suzuki4")
+            e1.record(gs[0].stream)
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            bt = [r for r in out["runs"] if r["precision"] == "fp64" and r["dt_multiplier"] == 1][0]["s"]
+            out["fp64_batch_vs_separate"] = {"steps": BATCH_EQ_STEPS, "separate_s": t, "batch_s": bt,
+                                             "speedup": t / bt, "launches_separate": len(gs)}
+        for g in gs:
+            g.close()
+        del gs
+        torch.cuda.empty_cache()
+    rows = []
+    for eps in (1e-3, 1e-4, 1e-5, 1e-6, 1e-8):
+        a = pick_fastest([r for r in out["runs"] if r["precision"] == "fp64"], eps)
+        b = pick_fastest([r for r in out["runs"] if r["precision"] == "fp32_mixed"], eps)
+        rows.append({"target_error": eps, "fp64": a, "fp32_mixed": b,
+                     "mixed_beats_fp64": None if a is None else (b is not None and b["s"] < a["s"]),
+                     "fp64_s_over_mixed_s": a["s"] / b["s"] if a and b else None})
+    out["at_equal_error"] = rows
     return out
 
 
@@ -764,7 +1105,7 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed propagate calls, as in the timed region (for ncu captures)")
     ap.add_argument("--profile-case", default="hh8_fp64",
-                    choices=["hh8_fp64", "atom_diatom", "hh7_fp32", "hh7_fp64"])
+                    choices=["hh8_fp64", "atom_diatom", "hh7_fp32", "hh7_fp64", "tc_dft16"])
     ap.add_argument("--headline-only", action="store_true", help="skip the secondary legs")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -807,7 +1148,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            g.propagate(1, HH_DT, HH_SCHEME)
+            g.propagate(HH_STEPS_PER_CALL, HH_DT, HH_SCHEME)
             e1.record(stream)
             times.append((e0, e1))
         torch.cuda.synchronize(dev)
@@ -816,12 +1157,12 @@ def main():
     g.sync()
     launches = g.launches - launches0
     ms = [a.elapsed_time(b) for a, b in times]
-    t_total, units = job_time_and_units(sum(ms) / 1e3, npts * args.steps, dist, device=dev)
+    t_total, units = job_time_and_units(sum(ms) / 1e3, npts * HH_STEPS_PER_CALL * args.steps, dist, device=dev)
     value = units / t_total
 
     # end to end through the C-ABI with host buffers: every iteration uploads
-    # the state from pinned host memory (mg_upload_u), propagates one step and
-    # reads the state back (mg_download_u)
+    # the state from pinned host memory (mg_upload_u), propagates
+    # HH_STEPS_PER_CALL time steps and reads the state back (mg_download_u)
     host = torch.empty(npts, dtype=torch.complex128, pin_memory=True)
     q, p, tt = g.download_u(host)
     barrier()
@@ -829,10 +1170,10 @@ def main():
     for _ in range(HH_E2E_ITERS):
         t0 = time.perf_counter()
         g.upload_u(host, q, p, tt)
-        g.propagate(1, HH_DT, HH_SCHEME)
+        g.propagate(HH_STEPS_PER_CALL, HH_DT, HH_SCHEME)
         q, p, tt = g.download_u(host)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = npts * world / statistics.median(e2e_t)
+    e2e_value = npts * HH_STEPS_PER_CALL * world / statistics.median(e2e_t)
     g.close()
     del g, host
     torch.cuda.empty_cache()
@@ -845,7 +1186,7 @@ def main():
     hbm_peak, hbm_src = peaks()
     flops_ps = algorithmic_flops_per_point_stage((HH_N,) * HH_D, HH_D)
     t_launch = statistics.mean(ms) / 1e3
-    ps = npts * HH_STAGES / t_launch
+    ps = npts * HH_STAGES * HH_STEPS_PER_CALL / t_launch
     achieved_tf = flops_ps * ps / 1e12
     achieved_gbs = algorithmic_bytes_per_point_stage() * ps / 1e9
     # the oracle on a bounded sample of the same model: one time step on 12^5,
@@ -883,8 +1224,12 @@ def main():
         secondary["other_workloads"] = other_workloads(mg, torch, dev, flush)
         secondary["adjoint"] = adjoint_leg(mg, torch, dev)
         secondary["batch"] = batch_leg(mg, torch, dev)
+        secondary["batch_equal_error"] = batch_equal_error_leg(mg, torch, dev, MEASURED["batch_knobs_fp32"])
+        secondary["mixed_equal_error"] = equal_error_leg(mg, torch, dev)
         secondary["error_vs_order"] = order_leg(mg, torch, dev)
         secondary["ensemble"] = ensemble_leg(mg, torch, dev)
+        secondary["dft16_tensor_cores"] = tc_dft16_leg(mg, torch, dev)
+        secondary["adaptive_vs_fixed"] = adaptive_vs_fixed_leg(mg, torch, dev)
         del flush
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -897,7 +1242,7 @@ def main():
         "roofline": {
             "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak(), "unit": "TFLOP/s",
             "frac": achieved_tf / fp64_peak(), "traffic": traffic_per_launch(),
-            "kernel": "k_propagate_short<double, 12> (persistent, one launch per time step)",
+            "kernel": f"k_propagate_short<double, 12> (persistent, one launch per {HH_STEPS_PER_CALL} time steps)",
             "flops_per_point_stage": flops_ps,
             "peak_source": "measured in this run: FP64 FMA rate (mg_probe_fma_rate, burst), "
                            f"nominal {FP64_PEAK_TFLOPS:.3f} = 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
@@ -909,8 +1254,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
                 "d2h_bytes_per_step": npts * 16,
-                "note": "mg_upload_u (pinned host psi) + mg_propagate + mg_download_u (pinned host psi) per "
-                        f"iteration, median of {HH_E2E_ITERS}"},
+                "note": f"mg_upload_u (pinned host psi) + mg_propagate ({HH_STEPS_PER_CALL} time steps) + "
+                        f"mg_download_u (pinned host psi) per iteration, median of {HH_E2E_ITERS}"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s": wall,

@@ -277,7 +277,9 @@ mg_status mg_probe_fma_rate(int precision, void* cuda_stream, double* tflops);
  * host complex FP64 (16 values each; post may be NULL for 1).  split = 1:
  * 3xTF32 split products (x = xb + xs, M = Mb + Ms, Xb Mb + Xb Ms + Xs Mb);
  * split = 2: BF16x3 (three bfloat16 terms each, six products); FP32
- * accumulation either way.  Synchronises cuda_stream; MG_ERR_TIMEOUT if a
+ * accumulation either way.  split = 0: the same lines through an FP32
+ * register DFT (4 x 4 with twiddles) on the FP32 units, the comparison for
+ * the tensor-core forms.  Synchronises cuda_stream; MG_ERR_TIMEOUT if a
  * tensor-core completion wait ran out (every wait is bounded). */
 mg_status mg_probe_tc_dft16(int split, int inverse, const void* d_x, void* d_y, int64_t nlines, const double* pre,
                             const double* post, void* cuda_stream);

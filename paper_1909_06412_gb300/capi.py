@@ -29,6 +29,7 @@ __all__ = [n for n in dir() if n.startswith("MG_")] + ["Propagator", "Batch", "M
                                                         "mg_scheme_coefficients", "mg_probe_fma_rate",
                                                         "mg_probe_expi", "mg_probe_tc_dft16"]
 
+
 _lib = None
 
 
@@ -158,17 +159,20 @@ def mg_probe_fma_rate(precision=MG_FP64, stream=None):
     return float(out[0])
 
 
-def mg_probe_tc_dft16(x, pre, post=None, split=1, inverse=False, stream=None):
+def mg_probe_tc_dft16(x, pre, post=None, split=1, inverse=False, stream=None, out=None):
     """The 16-point DFT with diagonal multipliers on the tensor cores
     (mg_probe_tc_dft16): x a CUDA complex64 tensor of shape (lines, 16);
     pre, post 16 complex values (post None for 1); split 1 = 3xTF32,
-    2 = BF16x3.  Returns y like x."""
+    2 = BF16x3, 0 = the FP32 register DFT for comparison.  Returns y like x
+    (written to out when given)."""
     import torch
 
     xx = x.contiguous()
     if xx.dtype != torch.complex64 or not xx.is_cuda or xx.shape[-1] != 16:
         raise ValueError("x must be a CUDA complex64 tensor of lines of 16 values")
-    y = torch.empty_like(xx)
+    y = torch.empty_like(xx) if out is None else out
+    if y.shape != xx.shape or y.dtype != xx.dtype or not y.is_contiguous():
+        raise ValueError("out must be a contiguous tensor like x")
     pr = np.ascontiguousarray(np.asarray(pre, dtype=np.complex128).reshape(16))
     po = None if post is None else np.ascontiguousarray(np.asarray(post, dtype=np.complex128).reshape(16))
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None

@@ -137,6 +137,50 @@ __global__ void __launch_bounds__(256, 1)
 
 template <int TC, bool INV> void* tc_kernel() { return (void*)k_tc_dft16<TC, INV>; }
 
+// The same lines through the FP32 register DFT (16 = 4 x 4 with twiddles, the
+// short-axis kernel's codelet form): the comparison for the tensor-core forms.
+static __device__ float2 g_tw16[16];  // e^{-2 pi i m / 16}, rounded to FP32
+
+template <bool INV>
+__global__ void __launch_bounds__(256)
+    k_reg_dft16(const float2* __restrict__ x, float2* __restrict__ y, int64_t nlines, int has_post) {
+  __shared__ float2 tw[16], mult[32];
+  if (threadIdx.x < 16) tw[threadIdx.x] = g_tw16[threadIdx.x];
+  if (threadIdx.x < 32) mult[threadIdx.x] = g_tc_mult[threadIdx.x];
+  __syncthreads();
+  for (int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; line < nlines;
+       line += (int64_t)gridDim.x * blockDim.x) {
+    float2 v[16], w[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(x[line * 16 + r], mult[r]);
+    // first stage: 4-point DFTs over n1 (input index 4 n1 + n2), twiddle W^(n2 k1)
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      float2 t[4];
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) t[n1] = v[4 * n1 + n2];
+      Dft<INV, 4, float2>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        const int m = n2 * k1;
+        w[n2 * 4 + k1] = m == 0 ? t[k1] : (INV ? cmulc(t[k1], tw[m]) : cmul(t[k1], tw[m]));
+      }
+    }
+    // second stage: 4-point DFTs over n2, output index k1 + 4 k2
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 t[4];
+#pragma unroll
+      for (int n2 = 0; n2 < 4; ++n2) t[n2] = w[n2 * 4 + k1];
+      Dft<INV, 4, float2>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) y[line * 16 + r] = has_post ? cmul(v[r], mult[16 + r]) : v[r];
+  }
+}
+
 }  // namespace
 }  // namespace mgk
 
@@ -144,13 +188,36 @@ using namespace mgk;
 
 extern "C" mg_status mg_probe_tc_dft16(int split, int inverse, const void* d_x, void* d_y, int64_t nlines,
                                        const double* pre, const double* post, void* cuda_stream) {
-  if (nlines < 0 || (nlines > 0 && (!d_x || !d_y)) || !pre || (split != 1 && split != 2)) return MG_ERR_ARG;
+  if (nlines < 0 || (nlines > 0 && (!d_x || !d_y)) || !pre || split < 0 || split > 2) return MG_ERR_ARG;
   if (nlines == 0) return MG_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   float2 m[32];
   for (int i = 0; i < 16; ++i) {
     m[i] = make_float2((float)pre[2 * i], (float)pre[2 * i + 1]);
     m[16 + i] = post ? make_float2((float)post[2 * i], (float)post[2 * i + 1]) : make_float2(1.f, 0.f);
+  }
+  if (split == 0) {
+    float2 tw[16];
+    for (int i = 0; i < 16; ++i) {
+      const double a = -2.0 * M_PI * i / 16.0;
+      tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    int dev = 0, sms = 0;
+    if (cudaMemcpyToSymbolAsync(g_tc_mult, m, sizeof(m), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(g_tw16, tw, sizeof(tw), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return MG_ERR_CUDA;
+    const int64_t want = (nlines + 255) / 256;
+    const int blocks = (int)(want < 8 * sms ? want : 8 * sms);
+    const float2* xp = (const float2*)d_x;
+    float2* yp = (float2*)d_y;
+    if (inverse)
+      k_reg_dft16<true><<<blocks, 256, 0, st>>>(xp, yp, nlines, post ? 1 : 0);
+    else
+      k_reg_dft16<false><<<blocks, 256, 0, st>>>(xp, yp, nlines, post ? 1 : 0);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return MG_ERR_CUDA;
+    return MG_OK;
   }
   void* fn = split == 1 ? (inverse ? tc_kernel<TC_TF32X3, true>() : tc_kernel<TC_TF32X3, false>())
                         : (inverse ? tc_kernel<TC_BF16X3, true>() : tc_kernel<TC_BF16X3, false>());

@@ -48,7 +48,7 @@ def test_fma_rate_probe(mg):
     assert r64 > 0 and r32 > r64
 
 
-@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("split", [0, 1, 2])
 @pytest.mark.parametrize("inverse", [False, True])
 @pytest.mark.parametrize("nlines", [1, 256, 1000, 40000])
 def test_tensor_core_dft16_against_fp64(mg, split, inverse, nlines):
