@@ -220,6 +220,7 @@ template <typename V, typename T> struct SSm {
   V* F;       // [D*n] per-axis potential factors
   V* Pt;      // [(D-1)*n*n] pair factors
   T* col;     // [5][D*n] f', g, g', h, h'
+  V* Tp;      // [ngroups][n][n] products of the first two multipliers a group's transform meets
   V* reg[3];
   // tensor-core DFT (ShortPlan::tc != 0): B operands of the group's axes,
   // A operands of the two warpgroups, their MMA barriers, the TMEM address
@@ -264,6 +265,7 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   m.F = (V*)take(sizeof(V) * TT);
   m.Pt = (V*)take(sizeof(V) * (P.D - 1) * n * n);
   m.col = (T*)take(sizeof(T) * 5 * TT);
+  m.Tp = (V*)take(sizeof(V) * SP.ngroups * n * n);
   // chunk regions start on 1024-byte boundaries (the period of the 128-byte
   // swizzle of the tensor copies)
   for (int r = 0; r < 3; ++r) {
@@ -404,6 +406,26 @@ __device__ void load_demod_short(const Plan& P, const ShortPlan& SP, const Smem<
   for (int e = threadIdx.x; e < P.tab_total; e += blockDim.x) {
     S.tA[e] = from_d2<V>(__ldcg(SP.tabB + e));
     S.tAi[e] = from_d2<V>(__ldcg(SP.tabC + e));
+  }
+}
+
+// A diagonal multiplier along one axis commutes with the DFTs along the
+// others, so the multipliers of the first two axes a group's transform meets
+// are applied together in the first axis's loop, and the second axis's loop
+// multiplies by nothing: one complex multiply per point saved per group of two
+// or more axes, each way.  Forward: the group's last axis, then the one before
+// it (tables tA); inverse: its first axis, then the next (tables tK).
+// Tp[g][jo][r] = t[a1][r] t[a2][jo], a1 the first axis, a2 the second.
+template <typename V, typename T>
+__device__ void build_pairs(const ShortPlan& SP, const SSm<V, T>& S, bool inv) {
+  const int n = SP.n, nn = n * n;
+  const V* t = inv ? S.s.tK : S.s.tA;
+  for (int e = threadIdx.x; e < SP.ngroups * nn; e += blockDim.x) {
+    const int gi = e / nn, jo = (e - gi * nn) / n, r = e % n;
+    const int g = SP.grp[gi].g, l0 = SP.grp[gi].l0;
+    if (g < 2) continue;
+    const int a1 = inv ? l0 : l0 + g - 1, a2 = inv ? l0 + 1 : l0 + g - 2;
+    S.Tp[e] = cmul(t[a1 * n + r], t[a2 * n + jo]);
   }
 }
 
@@ -748,6 +770,11 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       const Div16 dlo((unsigned)nlo), dhi((unsigned)nhi), dwp((unsigned)WP);
       const V* pre = (INV ? S.s.tK : S.s.tA) + a * N;
       const V* post = (INV && POST) ? S.s.tAi + a * N : nullptr;
+      // multipliers: the pair product (build_pairs) on the group's first axis,
+      // none on its second, the axis's own table after that
+      const int pm = (g >= 2 && kk < 2) ? kk + 1 : 0;
+      const V* tpg = S.Tp + gi * N * N;
+      const Div16 dsec((unsigned)ipow<N>(g >= 2 ? g - 2 : 0));
       // element addressing: linear (base + r * stride) except for the swizzled
       // layout along its last two axes
       const int kind = (lay == 1 && k == g - 1) ? 2 : ((lay == 1 && k == g - 2) ? 1 : 0);
@@ -831,8 +858,16 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
 #pragma unroll
           for (int r = 0; r < N; ++r) x[r] = V{(T)v[2 * r], (T)v[2 * r + 1]};
         } else {
+          if (pm == 1) {
+            // the coordinate of the line along the group's second axis
+            const int jo = INV ? (int)dsec((unsigned)lo) : hi % N;
+            const V* tp = tpg + jo * N;
 #pragma unroll
-          for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
+            for (int r = 0; r < N; ++r) x[r] = cmul(x[r], tp[r]);
+          } else if (pm == 0) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) x[r] = cmul(x[r], pre[r]);
+          }
           LineDft<INV, N, V>::run(x, tw);
           if (post) {
 #pragma unroll
@@ -1020,6 +1055,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     S.s.tAi[e] = from_d2<V>(make_double2(a.x, -a.y));
   }
   __syncthreads();
+  build_pairs(SP, S, false);
+  __syncthreads();
   const double* gam = B.gamma;
 
   if (RN.lead_v) {
@@ -1042,6 +1079,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     build_demod_short(P, SP, S.s, 0);  // the state is still u
     if (!grid_sync(B, &sflag)) return;
     load_demod_short(P, SP, S.s);
+    __syncthreads();
+    build_pairs(SP, S, false);
     __syncthreads();
   }
 
@@ -1075,6 +1114,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     if (hasv) load_v_short(P, SP, B, S);
     if (threadIdx.x < D) sc[SC_Q + threadIdx.x] = sc[SC_QN + threadIdx.x];
     __syncthreads();
+    build_pairs(SP, S, true);
+    __syncthreads();
     // inverse transform from the group of axis 0; the potential substep is
     // fused into the pass over the group that holds the last axis
     for (int gi = ng - 1; gi >= 0; --gi) {
@@ -1099,6 +1140,8 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
         build_demod_short(P, SP, S.s, 1);  // the state carries A(p_old)
         if (!grid_sync(B, &sflag)) return;
         load_demod_short(P, SP, S.s);
+        __syncthreads();
+        build_pairs(SP, S, false);
         __syncthreads();
       }
     }

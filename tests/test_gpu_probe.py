@@ -67,3 +67,34 @@ def test_tensor_core_dft16_against_fp64(mg, split, inverse, nlines):
     err = np.abs(y - ref).max() / np.abs(ref).max()
     # FP32-level: the split products keep 21-24 significant bits per operand
     assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("split", [0, 1, 2])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_tensor_core_dft16_is_the_oracles_transform(mg, split, sign):
+    # eq:fourier_pos_to_mom_b on a 16-point axis: f_KJ = N^-1/2 e^{-2 pi i kj/N}
+    # e^{-i t_KJ/hbar}, with t_KJ of eq:t_definition separating into a J part,
+    # a K part and a constant; the inverse (sign +1) is its adjoint.  The lines
+    # through the tensor-core (or register) 16-point DFT with those diagonal
+    # factors, element by element against the oracle's transform of each line.
+    import oracle
+
+    n, dq, hbar = 16, 0.37, 1.0
+    q, p = 0.83, -1.9
+    dp = 2 * np.pi * hbar / (n * dq)
+    j = np.arange(n)
+    c0 = (p - dp * n / 2) * (q - dq * n / 2)
+    jpart = np.exp(-1j * (p * dq - np.pi * hbar) * j / hbar)
+    kpart = np.exp(-1j * ((q * dp - np.pi * hbar) * j + c0) / hbar)
+    if sign == -1:
+        pre, post = jpart / np.sqrt(n), kpart
+    else:
+        pre, post = np.conj(kpart) / np.sqrt(n), np.conj(jpart)
+    g = inputs.rng(5150 + split)
+    nl = 300
+    x = (g.standard_normal((nl, n)) + 1j * g.standard_normal((nl, n))).astype(np.complex64)
+    y = mg.mg_probe_tc_dft16(torch.from_numpy(x).cuda(), pre, post, split, sign == 1).cpu().numpy()
+    o = oracle.Grid((n,), (dq,), hbar=hbar)
+    ref = np.stack([o.apply_f([q], [p], x[i].astype(np.complex128), sign) for i in range(nl)])
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
