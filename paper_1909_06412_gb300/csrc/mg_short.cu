@@ -220,7 +220,7 @@ template <typename V, typename T> struct SSm {
   V* F;       // [D*n] per-axis potential factors
   V* Pt;      // [(D-1)*n*n] pair factors
   T* col;     // [5][D*n] f', g, g', h, h'
-  V* Tp;      // [ngroups][n][n] products of the first two multipliers a group's transform meets
+  V* Tp;      // [ngroups][n][n+1] products of the first two multipliers a group's transform meets
   V* reg[3];
   // tensor-core DFT (ShortPlan::tc != 0): B operands of the group's axes,
   // A operands of the two warpgroups, their MMA barriers, the TMEM address
@@ -265,7 +265,7 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   m.F = (V*)take(sizeof(V) * TT);
   m.Pt = (V*)take(sizeof(V) * (P.D - 1) * n * n);
   m.col = (T*)take(sizeof(T) * 5 * TT);
-  m.Tp = (V*)take(sizeof(V) * SP.ngroups * n * n);
+  m.Tp = (V*)take(sizeof(V) * SP.ngroups * n * (n + 1));
   // chunk regions start on 1024-byte boundaries (the period of the 128-byte
   // swizzle of the tensor copies)
   for (int r = 0; r < 3; ++r) {
@@ -358,8 +358,11 @@ __device__ void build_v_short(const Plan& P, const ShortPlan& SP, const Bufs& B,
       double ca[6], cb[6];
       chain_terms(P, a, x, ca);
       chain_terms(P, a + 1, y, cb);
+      // the last pair's factor carries the last axis's own term too: the
+      // potential sweep runs along that axis and multiplies by one factor
+      const double th = a == P.D - 2 ? fma(ca[4], cb[2], cb[0]) : ca[4] * cb[2];
       double sn, cs;
-      expi_prec(P.prec, sgh * ca[4] * cb[2], S.sct, sn, cs);
+      expi_prec(P.prec, sgh * th, S.sct, sn, cs);
       __stcg(SP.tabP + e, P.prec ? round_unit_f32(cs, sn, 1.0) : make_double2(cs, sn));
     }
   }
@@ -415,7 +418,9 @@ __device__ void load_demod_short(const Plan& P, const ShortPlan& SP, const Smem<
 // multiplies by nothing: one complex multiply per point saved per group of two
 // or more axes, each way.  Forward: the group's last axis, then the one before
 // it (tables tA); inverse: its first axis, then the next (tables tK).
-// Tp[g][jo][r] = t[a1][r] t[a2][jo], a1 the first axis, a2 the second.
+// Tp[g][jo][r] = t[a1][r] t[a2][jo], a1 the first axis, a2 the second; rows
+// padded to n + 1 entries, so that the lines of a warp (one jo each) read
+// different banks.
 template <typename V, typename T>
 __device__ void build_pairs(const ShortPlan& SP, const SSm<V, T>& S, bool inv) {
   const int n = SP.n, nn = n * n;
@@ -425,7 +430,7 @@ __device__ void build_pairs(const ShortPlan& SP, const SSm<V, T>& S, bool inv) {
     const int g = SP.grp[gi].g, l0 = SP.grp[gi].l0;
     if (g < 2) continue;
     const int a1 = inv ? l0 : l0 + g - 1, a2 = inv ? l0 + 1 : l0 + g - 2;
-    S.Tp[e] = cmul(t[a1 * n + r], t[a2 * n + jo]);
+    S.Tp[(gi * n + jo) * (n + 1) + r] = cmul(t[a1 * n + r], t[a2 * n + jo]);
   }
 }
 
@@ -773,7 +778,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       // multipliers: the pair product (build_pairs) on the group's first axis,
       // none on its second, the axis's own table after that
       const int pm = (g >= 2 && kk < 2) ? kk + 1 : 0;
-      const V* tpg = S.Tp + gi * N * N;
+      const V* tpg = S.Tp + gi * N * (N + 1);
       const Div16 dsec((unsigned)ipow<N>(g >= 2 ? g - 2 : 0));
       // element addressing: linear (base + r * stride) except for the swizzled
       // layout along its last two axes
@@ -861,7 +866,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           if (pm == 1) {
             // the coordinate of the line along the group's second axis
             const int jo = INV ? (int)dsec((unsigned)lo) : hi % N;
-            const V* tp = tpg + jo * N;
+            const V* tp = tpg + jo * (N + 1);
 #pragma unroll
             for (int r = 0; r < N; ++r) x[r] = cmul(x[r], tp[r]);
           } else if (pm == 0) {
@@ -961,8 +966,8 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
             sg += lcg[r] * w;
             sfp += lcfp[r] * w;
             sgp += lcgp[r] * w;
-            V f = cmul(lf, fl[r]);
-            if (prow) f = cmul(f, prow[r]);
+            // prow already holds the last axis's own factor (build_v_short)
+            const V f = cmul(lf, prow ? prow[r] : fl[r]);
             reg[e] = cmul(xv, f);
           }
           acc.add(0, s0);

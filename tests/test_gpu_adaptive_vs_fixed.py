@@ -1,0 +1,83 @@
+"""The accuracy of grid adaptation as Sec. III measures it (Figs. 3 and 8): the
+adaptive-grid state against a fixed-grid reference on a larger grid, run with
+the same composition and time step on the GPU, compared through trigonometric
+interpolation of the sparser state onto the denser grid (tests/grid_distance).
+The fourth-order triple jump keeps these tests short; the benchmark runs the
+same comparisons with the tenth-order one to the paper's final times."""
+import numpy as np
+import pytest
+
+from tests import grid_distance as gd
+from tests import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1909_06412_gb300 as m
+
+    m.lib()
+    return m
+
+
+def grid_of(g):
+    _, q, p, _ = g.get_state(want_psi=False)
+    return {"N": list(g.N), "dq": list(g.dq), "q": list(q), "p": list(p)}
+
+
+def test_harmonic_adaptive_grid_matches_the_larger_fixed_grid(mg):
+    # Sec. III.A: 32^3 adaptive grid (Table I) against the 128^3 fixed grid
+    # with twice its q and p ranges, centred at the middle of the packet's
+    # sweep; the paper finds 5e-11 at t = 0 and 2e-10 at t_f
+    P = inputs.DUSCHINSKY3D
+
+    def make(N, dq, centre):
+        g = mg.Propagator(N, dq, minv=P["omega"])
+        g.set_potential(mg.MG_POT_HARMONIC, list(np.array(P["K"]).ravel()) + list(P["q0"]))
+        g.set_separable([("gauss", 0.0, 0.0, 1.0)] * 3, list(centre), [0.0] * 3)
+        return g
+
+    ga = make((32,) * 3, (0.4375,) * 3, (0.0,) * 3)
+    gf = make((128,) * 3, (0.21875,) * 3, P["q0"])
+    d0 = gd.distance(ga.get_state()[0], grid_of(ga), gf.get_state()[0], grid_of(gf))
+    assert d0 < 1e-10, d0
+    dt = 50.0 / 512
+    ga.propagate(64, dt, "yoshida4", mg.MG_TVT, mg.MG_GRID_ADAPTIVE)
+    gf.propagate(64, dt, "yoshida4", mg.MG_TVT, mg.MG_GRID_FIXED)
+    psi_a, sa = ga.get_state()[0], grid_of(ga)
+    psi_f, sf = gf.get_state()[0], grid_of(gf)
+    # the grid has moved well away from its start
+    assert np.abs(np.array(sa["q"])).max() > 3.0, sa["q"]
+    d = gd.distance(psi_a, sa, psi_f, sf)
+    assert d < 1e-9, d
+    assert np.abs(gd.mean_q(psi_a, sa) - gd.mean_q(psi_f, sf)).max() < 1e-9
+
+
+def test_scattering_adaptive_grid_outlasts_the_fixed_grid(mg):
+    # Sec. III.B: He-H2 on adaptive and fixed 128 x 128 grids against the
+    # fixed 128 x 2048 reference; the adaptive error stays small long after
+    # the packet has left the fixed grid
+    sj = [20.0, 0.158, 0.3]
+    fac = [("gauss", 0.0, 0.0, 1.0), ("gauss", 24.0, -3.56, np.sqrt(8.0))]
+
+    def make(N, lo2, hi2):
+        dq = (28.0 / N[0], (hi2 - lo2) / N[1])
+        g = mg.Propagator(N, dq, minv=(1.0, 1.5))
+        g.set_potential(mg.MG_POT_SECREST_JOHNSON, sj)
+        g.set_separable(fac, [0.0, lo2 + (N[1] // 2) * dq[1]], [0.0, -3.56])
+        return g
+
+    ga, gf, gr = make((128, 128), 0.0, 48.0), make((128, 128), 0.0, 48.0), make((128, 2048), -50.0, 400.0)
+    assert gr.tables_in_workspace == 3
+    ga.propagate(100, 0.1, "yoshida4", mg.MG_VTV, mg.MG_GRID_ADAPTIVE)
+    gf.propagate(100, 0.1, "yoshida4", mg.MG_VTV, mg.MG_GRID_FIXED)
+    gr.propagate(100, 0.1, "yoshida4", mg.MG_VTV, mg.MG_GRID_FIXED)
+    psi_r, sr = gr.get_state()[0], grid_of(gr)
+    da = gd.distance(ga.get_state()[0], grid_of(ga), psi_r, sr)
+    df = gd.distance(gf.get_state()[0], grid_of(gf), psi_r, sr)
+    assert da < 1e-4, da
+    assert df > 0.5, df
