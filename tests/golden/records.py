@@ -58,3 +58,18 @@ def read(name):
     rec["idx"] = np.array(idx, dtype=np.int64)
     rec["psi"] = np.array(vals)
     return rec
+
+
+def read_scalars(name):
+    """dict of the `key = values` lines of a stored record (arrays for
+    several values, floats for one)."""
+    rec = {}
+    with open(os.path.join(HERE, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#") or "=" not in line:
+                continue
+            k, v = (s.strip() for s in line.split("=", 1))
+            nums = [float(x) for x in v.split()]
+            rec[k] = np.array(nums) if len(nums) > 1 else nums[0]
+    return rec

@@ -9,6 +9,7 @@ import pytest
 
 from tests import grid_distance as gd
 from tests import inputs
+from tests.golden.records import read_scalars
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,8 +54,16 @@ def test_harmonic_adaptive_grid_matches_the_larger_fixed_grid(mg):
     # the grid has moved well away from its start
     assert np.abs(np.array(sa["q"])).max() > 3.0, sa["q"]
     d = gd.distance(psi_a, sa, psi_f, sf)
-    assert d < 1e-9, d
-    assert np.abs(gd.mean_q(psi_a, sa) - gd.mean_q(psi_f, sf)).max() < 1e-9
+    dq_mean = np.abs(gd.mean_q(psi_a, sa) - gd.mean_q(psi_f, sf)).max()
+    # the same two propagations by the FP64 oracle (stored record): the
+    # distance is the method's representation error at t = 6.25 (1.3e-9 with
+    # this fourth-order scheme), and the GPU reproduces it to roundoff
+    rec = read_scalars("adaptive_vs_fixed_duschinsky_yoshida4_64.txt")
+    assert abs(d - rec["distance"]) < 1e-12, (d, rec["distance"])
+    assert abs(dq_mean - rec["mean_q_distance"]) < 1e-12, (dq_mean, rec["mean_q_distance"])
+    assert np.abs(np.array(sa["q"]) - rec["q"]).max() < 1e-12
+    assert np.abs(np.array(sa["p"]) - rec["p"]).max() < 1e-12
+    assert d < 2e-9, d
 
 
 def test_scattering_adaptive_grid_outlasts_the_fixed_grid(mg):
