@@ -53,11 +53,13 @@ HH_REF_D = 4   # reference arm: one time step on 12^4 per timed step
 ADJ_STEPS = 200
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# DRAM bytes (read + write) of one headline propagate launch (one 12^8 time
-# step), from an ncu capture of the same launch on 12^7 scaled by 12 (the
-# traffic of a pass grows with the points it streams); valid only for the
-# kernel sources it was taken on (sha256 of the files below, concatenated).
-TRAFFIC_RECORD = {"kernel_sha256": "", "bytes_per_launch": None}
+# DRAM bytes (read + write) of one headline propagate launch (HH_STEPS_PER_CALL
+# time steps on 12^8), from an ncu capture of the same launch shape on 12^7
+# scaled by 12 (both plans make three group passes per transform, so the
+# traffic grows with the points streamed); valid only for the kernel sources
+# it was taken on (sha256 of the files below, concatenated).
+TRAFFIC_RECORD = {"kernel_sha256": "94f47f4eb63a036acb7c6f4a7282104a06c52d6c7faab5eb2480a140cb98a1f5",
+                  "bytes_per_launch": 1.757425824e12}  # (72.62 + 73.83) GB on 12^7 x 12
 KERNEL_SOURCES = ("mg_short.cu", "mg_short.h", "mg_device.cuh", "mg_plan.h")
 
 # FP64 peak from unit counts and clocks (152 SMs x 2 FP64 FMA/clk x 2 flop x
@@ -334,7 +336,7 @@ def run_profile(args):
     hh8_fp64 (default): the headline, 12^8 FP64, HH_STEPS_PER_CALL time steps
     per call as timed;
     hh7_fp64 / hh7_fp32: Henon-Heiles on 12^7 (FP64) / 16^7 (FP32) grids, the
-    small cases for full captures; atom_diatom: the 256 x 256 workload,
+    small cases for full captures, with the same time steps per call; atom_diatom: the 256 x 256 workload,
     STEPS_PER_CALL steps per call; tc_dft16: the standalone 16-point DFT on
     TC_PROFILE_LINES lines, register form then 3xTF32 then BF16x3."""
     import torch
@@ -360,7 +362,7 @@ def run_profile(args):
         n, D, prec = {"hh8_fp64": (12, 8, mg.MG_FP64), "hh7_fp32": (16, 7, mg.MG_FP32_MIXED),
                       "hh7_fp64": (12, 7, mg.MG_FP64)}[args.profile_case]
         g = hh_propagator(mg, n, D, prec)
-        k = HH_STEPS_PER_CALL if args.profile_case == "hh8_fp64" else 1
+        k = HH_STEPS_PER_CALL  # the launch shape of the timed region
         call = lambda: g.propagate(k, HH_DT, HH_SCHEME)
     for _ in range(args.warmup + args.steps):
         call()
