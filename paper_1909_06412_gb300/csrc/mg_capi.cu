@@ -239,7 +239,7 @@ bool short_smem(const Plan& P, ShortPlan& SP, int re) {
   const size_t TT = (size_t)P.tab_total, n = (size_t)SP.n;
   const size_t tabs = 5 * r16(vs * TT) + r16(sizeof(double2) * 256) + r16(sizeof(double) * 16 * 32) +
                       r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) + r16(sizeof(uint64_t) * 3) +
-                      r16(sizeof(unsigned) * 4) + r16(vs * (size_t)(P.D - 1) * n * n) + r16(ts * 5 * TT) +
+                      r16(sizeof(unsigned) * 4) + r16(vs * (size_t)(P.D - 1) * n * (n + 1)) + r16(ts * 5 * TT) +
                       r16(vs * (size_t)SP.ngroups * n * (n + 1));
   const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
   for (int nreg = 3; nreg >= 2; --nreg) {

@@ -218,7 +218,7 @@ __device__ void block_record(const Bufs& B, double* red, int slot, const LineAcc
 template <typename V, typename T> struct SSm {
   Smem<V> s;  // tw, tA, tAi, tK, sct, fin, sc, red (the fields the shared helpers use)
   V* F;       // [D*n] per-axis potential factors
-  V* Pt;      // [(D-1)*n*n] pair factors
+  V* Pt;      // [(D-1)*n][n+1] pair factors, rows padded (see load_v_short)
   T* col;     // [5][D*n] f', g, g', h, h'
   V* Tp;      // [ngroups][n][n+1] products of the first two multipliers a group's transform meets
   V* reg[3];
@@ -263,7 +263,7 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   s.tb = nullptr;
   s.li = nullptr;
   m.F = (V*)take(sizeof(V) * TT);
-  m.Pt = (V*)take(sizeof(V) * (P.D - 1) * n * n);
+  m.Pt = (V*)take(sizeof(V) * (P.D - 1) * n * (n + 1));
   m.col = (T*)take(sizeof(T) * 5 * TT);
   m.Tp = (V*)take(sizeof(V) * SP.ngroups * n * (n + 1));
   // chunk regions start on 1024-byte boundaries (the period of the 128-byte
@@ -443,7 +443,11 @@ __device__ void load_v_short(const Plan& P, const ShortPlan& SP, const Bufs& B, 
 #pragma unroll
     for (int k = 0; k < 5; ++k) S.col[k * TT + e] = (T)__ldcg(B.tabV + k * TT + e);
   }
-  for (int e = threadIdx.x; e < nP; e += blockDim.x) S.Pt[e] = from_d2<V>(__ldcg(SP.tabP + e));
+  // rows of the pair factors padded to n + 1 entries: the potential sweep's
+  // threads read one row each (their own coordinate on axis D-2) at the same
+  // column, which falls into different banks this way (unpadded, the rows of
+  // a 16-point FP32 table are 128 bytes apart: one bank for all of them)
+  for (int e = threadIdx.x; e < nP; e += blockDim.x) S.Pt[e + e / n] = from_d2<V>(__ldcg(SP.tabP + e));
 }
 
 // ---------------------------------------------------------------------------
@@ -947,8 +951,8 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           if (pairs) {
 #pragma unroll
             for (int b = 0; b < MAXD - 2; ++b)
-              if (b < D - 2) lf = cmul(lf, S.Pt[(b * N + j[b]) * N + j[b + 1]]);
-            prow = S.Pt + ((D - 2) * N + jm) * N;
+              if (b < D - 2) lf = cmul(lf, S.Pt[(b * N + j[b]) * (N + 1) + j[b + 1]]);
+            prow = S.Pt + ((D - 2) * N + jm) * (N + 1);
           }
           const V* fl = S.F + (D - 1) * N;
           T s0 = 0, sg = 0, sfp = 0, sgp = 0;
@@ -957,18 +961,30 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           const T* lcg = cg + (D - 1) * N;
           const T* lcfp = cfp + (D - 1) * N;
           const T* lcgp = cgp + (D - 1) * N;
-#pragma unroll 4
-          for (int r = 0; r < N; ++r) {
-            const int e = TMA ? swz(R, r) : base + r;
-            V xv = reg[e];
+          // one point: its moments and its phase factor (prow already holds
+          // the last axis's own factor, build_v_short)
+          auto point = [&](int r, V xv) {
             const T w = xv.x * xv.x + xv.y * xv.y;
             s0 += w;
             sg += lcg[r] * w;
             sfp += lcfp[r] * w;
             sgp += lcgp[r] * w;
-            // prow already holds the last axis's own factor (build_v_short)
-            const V f = cmul(lf, prow ? prow[r] : fl[r]);
-            reg[e] = cmul(xv, f);
+            return cmul(xv, cmul(lf, prow ? prow[r] : fl[r]));
+          };
+          if constexpr (TMA) {
+            // swizzled rows: two points per 16-byte access (8-byte accesses
+            // would put four threads of a warp on each bank)
+#pragma unroll 2
+            for (int cp = 0; cp < N / 2; ++cp) {
+              float4* q = reinterpret_cast<float4*>(reg + swz(R, 2 * cp));
+              const float4 v2 = *q;
+              const V y0 = point(2 * cp, V{(T)v2.x, (T)v2.y});
+              const V y1 = point(2 * cp + 1, V{(T)v2.z, (T)v2.w});
+              *q = make_float4((float)y0.x, (float)y0.y, (float)y1.x, (float)y1.y);
+            }
+          } else {
+#pragma unroll 4
+            for (int r = 0; r < N; ++r) reg[base + r] = point(r, reg[base + r]);
           }
           acc.add(0, s0);
           // axes whose derivative does not involve the line's coordinate
