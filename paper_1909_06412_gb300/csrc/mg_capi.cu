@@ -237,14 +237,19 @@ bool short_smem(const Plan& P, ShortPlan& SP, int re) {
   const size_t vs = P.prec == 0 ? sizeof(double2) : sizeof(float2);
   const size_t ts = P.prec == 0 ? sizeof(double) : sizeof(float);
   const size_t TT = (size_t)P.tab_total, n = (size_t)SP.n;
-  const size_t tabs = 5 * r16(vs * TT) + r16(sizeof(double2) * 256) + r16(sizeof(double) * 16 * 32) +
-                      r16(sizeof(double) * PSTRIDE) + r16(sizeof(double) * SCALARS) + r16(sizeof(uint64_t) * 3) +
-                      r16(sizeof(unsigned) * 4) + r16(vs * (size_t)(P.D - 1) * n * (n + 1)) + r16(ts * 5 * TT) +
+  // the sincos table only for FP64 (the FP32 phases use sincosf); one
+  // 16-value record per warp
+  const size_t tabs = 5 * r16(vs * TT) + (P.prec == 0 ? r16(sizeof(double2) * 256) : 0) +
+                      r16(sizeof(double) * 16 * (size_t)(SP.threads / 32)) + r16(sizeof(double) * PSTRIDE) +
+                      r16(sizeof(double) * SCALARS) + r16(sizeof(uint64_t) * 3) + r16(sizeof(unsigned) * 4) +
+                      r16(vs * (size_t)(P.D - 1) * n * (n + 1)) + r16(ts * 5 * TT) +
                       r16(vs * (size_t)SP.ngroups * n * (n + 1));
   const size_t cap = 227 * 1024 - 1024;  // dynamic shared memory, with room for the static part
+  const size_t rb = r16(vs * (size_t)re);
   for (int nreg = 3; nreg >= 2; --nreg) {
-    // + up to 1008 bytes per region to start it on a 1024-byte boundary
-    const size_t total = tabs + (size_t)nreg * (r16(vs * (size_t)re) + 1008) + tcb;
+    // + up to 1008 bytes per region to start it on a 1024-byte boundary;
+    // regions of whole kilobytes need that only before the first
+    const size_t total = tabs + (rb % 1024 == 0 ? 1008 + (size_t)nreg * rb : (size_t)nreg * (rb + 1008)) + tcb;
     if (total <= cap) {
       SP.region_elems = re;
       SP.nreg = nreg;

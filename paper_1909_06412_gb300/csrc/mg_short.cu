@@ -254,8 +254,10 @@ __device__ SSm<V, T> carve_short(const Plan& P, const ShortPlan& SP, unsigned ch
   s.tv = nullptr;
   s.tc = nullptr;
   s.te = nullptr;
-  s.sct = (double2*)take(sizeof(double2) * 256);
-  s.red = (double*)take(sizeof(double) * 16 * 32);
+  // the sincos table only for FP64 (expi_prec uses sincosf for FP32); one
+  // 16-value record per warp (block_record)
+  s.sct = P.prec ? nullptr : (double2*)take(sizeof(double2) * 256);
+  s.red = (double*)take(sizeof(double) * 16 * (blockDim.x >> 5));
   s.fin = (double*)take(sizeof(double) * PSTRIDE);
   s.sc = (double*)take(sizeof(double) * SC_N);
   s.mbar = (uint64_t*)take(sizeof(uint64_t) * 3);
@@ -583,6 +585,7 @@ __device__ __forceinline__ void tma_store(const void* tm, int rank, const void* 
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
@@ -709,6 +712,10 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   // (prefetch of the next set's first chunk; its second chunk is loaded into
   // X as soon as the set is stored).
   constexpr bool PAIR = !TMA && sizeof(T) == 8 && N == 12;
+  // prefetch distance: cp.async copies run nreg - 1 chunks ahead; tensor
+  // copies one chunk ahead, so that with three regions the next load never
+  // waits for the store issued just before it
+  const int pd = TMA ? 1 : nreg - 1;
   int rx = 0, ry = 1, rz = 2;
   if (PAIR) {
     for (int s = 0; s < 2; ++s) {
@@ -716,7 +723,7 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       cp_commit();
     }
   } else {
-    for (int s = 0; s < nreg - 1; ++s) {
+    for (int s = 0; s < pd; ++s) {
       if (TMA) {
         if (threadIdx.x == 0 && s < mine)
           tma_chunk(SP, G, gi, blockIdx.x + (int64_t)s * gridDim.x, region(S, s), S.s.mbar + s, false);
@@ -734,11 +741,15 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
       cp_wait<1>();
       __syncthreads();
     } else {
-      const int64_t i2 = i + nreg - 1;
+      const int64_t i2 = i + pd;
       const int r2 = (int)(i2 % nreg);
       if (TMA) {
         if (threadIdx.x == 0 && i2 < mine) {
-          bulk_wait_read0();  // the store that last read region r2 is done with it
+          // the store that last read region r2 is done with it: with three
+          // regions that store was issued two sets ago and the one of the
+          // last set may still be reading its own region
+          if (nreg == 3) bulk_wait_read1();
+          else bulk_wait_read0();
           fence_proxy_async();
           tma_chunk(SP, G, gi, blockIdx.x + i2 * gridDim.x, region(S, r2), S.s.mbar + r2, false);
         }
@@ -1066,7 +1077,7 @@ __global__ void __launch_bounds__(short_threads(sizeof(T) == 4, N), 1)
     sc[SC_Q + threadIdx.x] = __ldcg(B.ctrl + threadIdx.x);
     sc[SC_P + threadIdx.x] = __ldcg(B.ctrl + 8 + threadIdx.x);
   }
-  load_tables(P, B, S.s, LT_TW | LT_SCT);
+  load_tables(P, B, S.s, P.prec ? LT_TW : (LT_TW | LT_SCT));
   if (TMA) init_mbarriers(S.s);
   // the state enters as u: forward multiplier A/N = conj(conj(A)/N), final
   // post-multiplier conj(A), both exact conversions of the context's tables
