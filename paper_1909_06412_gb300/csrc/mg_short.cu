@@ -175,6 +175,8 @@ template <> struct LineAcc<double> {
     for (int k = 0; k < MAXD + 1; ++k)
       if (k == i) a[k] += x;
   }
+  // slot k of o into slot i (known only at run time)
+  __device__ __forceinline__ void merge_rt(int i, const LineAcc& o, int k) { add_rt(i, o.a[k]); }
 };
 template <> struct LineAcc<float> {
   float s[MAXD + 1], c[MAXD + 1];
@@ -188,6 +190,10 @@ template <> struct LineAcc<float> {
 #pragma unroll
     for (int k = 0; k < MAXD + 1; ++k)
       if (k == i) two_sum_acc(s[k], c[k], x);
+  }
+  __device__ __forceinline__ void merge_rt(int i, const LineAcc& o, int k) {
+    add_rt(i, o.s[k]);
+    add_rt(i, o.c[k]);
   }
 };
 
@@ -682,6 +688,10 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
   unsigned parity = TMA ? *S.s.mphase : 0u;
   LineAcc<T> acc;
   acc.zero();
+  // the potential sweep's gradient components of axes D-2 and D-1 (slots 0,
+  // 1), whose index is known only at run time: folded into acc once per pass
+  LineAcc<T> accv;
+  accv.zero();
   unsigned tmem = 0, tcpar = 0;
   if constexpr (TCM != TC_NONE && MODE != SM_VONLY) {
     static_assert(sizeof(T) == 4 && N == 16 && TMA, "tensor-core DFTs: FP32, 16-point lines, TMA copies");
@@ -967,8 +977,6 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           }
           const V* fl = S.F + (D - 1) * N;
           T s0 = 0, sg = 0, sfp = 0, sgp = 0;
-          // element by element from shared memory: nothing of the line is
-          // held in registers
           const T* lcg = cg + (D - 1) * N;
           const T* lcfp = cfp + (D - 1) * N;
           const T* lcgp = cgp + (D - 1) * N;
@@ -983,16 +991,43 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
             return cmul(xv, cmul(lf, prow ? prow[r] : fl[r]));
           };
           if constexpr (TMA) {
-            // swizzled rows: two points per 16-byte access (8-byte accesses
-            // would put four threads of a warp on each bank)
-#pragma unroll 2
+            // the whole line in registers (swizzled rows: two points per
+            // 16-byte access; 8-byte accesses would put four threads of a
+            // warp on each bank), its points independent of one another, the
+            // sums over them in two halves
+            V xs[N];
+#pragma unroll
             for (int cp = 0; cp < N / 2; ++cp) {
-              float4* q = reinterpret_cast<float4*>(reg + swz(R, 2 * cp));
-              const float4 v2 = *q;
-              const V y0 = point(2 * cp, V{(T)v2.x, (T)v2.y});
-              const V y1 = point(2 * cp + 1, V{(T)v2.z, (T)v2.w});
-              *q = make_float4((float)y0.x, (float)y0.y, (float)y1.x, (float)y1.y);
+              const float4 v2 = *reinterpret_cast<const float4*>(reg + swz(R, 2 * cp));
+              xs[2 * cp] = V{(T)v2.x, (T)v2.y};
+              xs[2 * cp + 1] = V{(T)v2.z, (T)v2.w};
             }
+            T h0 = 0, hg = 0, hfp = 0, hgp = 0;
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+              const T w = xs[r].x * xs[r].x + xs[r].y * xs[r].y;
+              if (r < N / 2) {
+                s0 += w;
+                sg += lcg[r] * w;
+                sfp += lcfp[r] * w;
+                sgp += lcgp[r] * w;
+              } else {
+                h0 += w;
+                hg += lcg[r] * w;
+                hfp += lcfp[r] * w;
+                hgp += lcgp[r] * w;
+              }
+              xs[r] = cmul(xs[r], cmul(lf, prow ? prow[r] : fl[r]));
+            }
+            s0 += h0;
+            sg += hg;
+            sfp += hfp;
+            sgp += hgp;
+#pragma unroll
+            for (int cp = 0; cp < N / 2; ++cp)
+              *reinterpret_cast<float4*>(reg + swz(R, 2 * cp)) =
+                  make_float4((float)xs[2 * cp].x, (float)xs[2 * cp].y, (float)xs[2 * cp + 1].x,
+                              (float)xs[2 * cp + 1].y);
           } else {
 #pragma unroll 4
             for (int r = 0; r < N; ++r) reg[base + r] = point(r, reg[base + r]);
@@ -1009,8 +1044,8 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
           {
             const int b = D - 2;  // D >= 3
             const T gb2 = (cfp[b * N + jm] + ch[(b - 1) * N + jm2] * cgp[b * N + jm]) * s0 + chp[b * N + jm] * sg;
-            acc.add_rt(1 + b, gb2);
-            acc.add_rt(D, sfp + ch[b * N + jm] * sgp);
+            accv.add(0, gb2);
+            accv.add(1, sfp + ch[b * N + jm] * sgp);
           }
         }
       }
@@ -1052,6 +1087,10 @@ __device__ __noinline__ void short_pass(const Plan& P, const ShortPlan& SP, cons
     __syncthreads();
     tc_fence_after();
     tc_dealloc(tmem);
+  }
+  if (MODE == SM_V || MODE == SM_VONLY) {
+    acc.merge_rt(D - 1, accv, 0);
+    acc.merge_rt(D, accv, 1);
   }
   if (MODE != SM_NONE) block_record<T>(B, S.s.red, slot, acc, D + 1);
 }
