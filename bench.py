@@ -50,7 +50,7 @@ HH_STEPS_PER_CALL = 3  # time steps per timed call: 3 x 5 stages, 16 kinetic uni
 HH_E2E_ITERS = 5
 HH_CPU_D = 5   # oracle sample: the same model on 12^5, one time step
 HH_REF_D = 4   # reference arm: one time step on 12^4 per timed step
-ADJ_STEPS = 200
+ADJ_STEPS = 2000  # the full length of the gradient workload
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM bytes (read + write) of one headline propagate launch (HH_STEPS_PER_CALL
@@ -492,7 +492,7 @@ def adjoint_leg(mgmod, torch, dev):
     rbar = mgmod.mg_morse_mean(POT[0], POT[1], POT[2], 0.5 * AMU)
     om = np.array([1.0, 1.2, 1.5])
     cases = [
-        ("atom-diatom 128x128 FP64, yoshida6, dt=1 a.u.", (128, 128), (0.16, 0.08), MINV,
+        ("atom-diatom 128x128 FP64, yoshida6, dt=1 a.u.", (128, 128), (0.08, 0.08), MINV,
          mgmod.MG_POT_ATOM_DIATOM, POT, initial(mgmod)[0], [8.0, rbar], [-10.0, 0.0], 1.0),
         ("3D harmonic 64^3 FP64, yoshida6, dt=0.01", (64, 64, 64), (0.3,) * 3, (1.0, 1.0, 1.0),
          mgmod.MG_POT_HARMONIC, list(np.diag(om ** 2).ravel()) + [0.0] * 3,

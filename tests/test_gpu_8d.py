@@ -53,6 +53,33 @@ def test_henon_heiles_4d_vs_oracle(mg, n, prec, tol):
     assert np.abs(q - q_o).max() < max(tol, 1e-12) and np.abs(p - p_o).max() < max(tol, 1e-12)
 
 
+@pytest.mark.parametrize("n,prec,tol", [(12, 0, 1e-12), (16, 0, 1e-12), (16, 1, 3e-4)])
+def test_henon_heiles_4d_500_steps_vs_stored_oracle(mg, n, prec, tol):
+    # the 8D workload's length (500 suzuki4 steps, dt = 0.01) on 4D grids,
+    # against the oracle's stored run (tests/golden/make_hh4_500.py), at its
+    # 1024 stored points (each within tol of the L2 norm of psi) and on the
+    # grid centres; the FP32 path's error after 500 steps is 1.4e-4 relative
+    # L2 (measured), stated here as the bound 3e-4
+    from tests.golden import records
+
+    D = 4
+    rec = records.read(f"hh_{n}p4_suzuki4_500.txt")
+    dq = np.sqrt(2 * np.pi / n)
+    g = mg.Propagator((n,) * D, (dq,) * D, precision=prec)
+    g.set_potential(mg.MG_POT_HENON_HEILES, [LAM])
+    g.set_separable([("gauss", 2.0, 0.0, 1.0)] * D, [2.0] * D, [0.0] * D)
+    g.propagate(500, 0.01, "suzuki4")
+    _, q, p, _ = g.get_state(want_psi=False)
+    ct = tol if prec == 0 else 1e-4
+    assert np.abs(q - rec["q"]).max() < ct * max(1.0, np.abs(rec["q"]).max()), (q, rec["q"])
+    assert np.abs(p - rec["p"]).max() < ct * max(1.0, np.abs(rec["p"]).max()), (p, rec["p"])
+    u = g.psi.view(torch.complex128 if prec == 0 else torch.complex64)
+    vals = u[torch.from_numpy(rec["idx"]).to(u.device)].to(torch.complex128).cpu().numpy() / np.sqrt(dq ** D)
+    d = np.abs(vals - rec["psi"]).max()
+    assert d < tol * rec["psi_l2"], d / rec["psi_l2"]
+    g.close()
+
+
 def full_size(mg, n, prec):
     D = 8
     dq = np.sqrt(2 * np.pi / n)
