@@ -520,7 +520,9 @@ def adjoint_leg(mgmod, torch, dev):
         tf, ta = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
         out.append({"workload": name, "steps": ADJ_STEPS, "forward_s": tf, "adjoint_s": ta,
                     "adjoint_over_forward": ta / tf,
-                    "note": "adjoint_s includes the host-side norm readout and cotangent upload of mg_adjoint"})
+                    "note": "adjoint_s includes the host-side norm readout and cotangent upload of mg_adjoint",
+                    "scope": "mg_adjoint: FP64 grids resident in the CTAs' shared memory, harmonic and "
+                             "atom-diatom potentials"})
         g.close()
         del g
         torch.cuda.empty_cache()
